@@ -1,0 +1,36 @@
+"""Plain FP64 CPU oracle for the Wilson-Dirac hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this package; only
+the tests, the smoke check and the benchmark's CPU-baseline leg call it.  It
+shares no code with the CUDA path: it works on canonical-layout numpy arrays
+with whole-lattice shifts and einsum, in float64/complex128, with no blocking,
+fusion or reordering beyond the definitions it cites.
+
+The paper (Kamleh, "Evolving the COLA software library", Lattice 2022) names
+the fermion-matrix inverter, the conjugate-gradient solver with 32-bit inner
+and 64-bit outer precision (Fig. 2 discussion) and Hybrid Monte Carlo, but
+writes no formula.  The operator, basis, boundary phases, even-odd split,
+CG recurrence and force therefore follow the standard lattice-QCD
+definitions, each stated where it is coded:
+
+  wilson.py  gamma matrices, hopping term H, D = 1 - kappa H, H^dagger,
+             even-odd blocks and the Schur operator Mhat, sampled-site H
+  solve.py   Hestenes-Stiefel CG with true-residual confirmation, the
+             even-odd normal-equation solve, dense matrices for brute force
+  force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
+
+Pins (tests/test_oracle_*.py, run without a GPU): gamma algebra; the free
+field closed form (plane waves and the full D^dag D spectrum); gamma5
+hermiticity and the adjoint identity; gauge covariance under random SU(3)
+transformations; brute-force dense solves on 2^4; the Schur identity between
+the even-odd and full solves; the force against central finite differences of
+an exactly computed action and against the closed form S = |eta|^2 at
+phi = D^dag eta.  Every function here is pinned by at least one of them.
+"""
+from .wilson import (  # noqa: F401
+    GAMMA, GAMMA5, IDENTITY4, parity_of_sites, even_mask, phased_links, hop,
+    dirac, dirac_dag, hop_block, mhat, mhat_dag, mdagm_full, mdagm_eo,
+    hop_sites, gamma5_apply,
+)
+from .solve import cg, solve_normal_full, solve_normal_eo, solve_dirac_eo, dense_matrix  # noqa: F401
+from .force import GELL_MANN, T_GEN, force_coeffs, dirac_link_grad, link_variation  # noqa: F401
