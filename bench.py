@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Wilson-Dirac hot path (one JSON line on stdout).
+
+Workload (default): mixed-precision even-odd CG on a 32^3x64 lattice,
+kappa = 0.1245, links exp(0.25 i H), Gaussian source, FP16 per-site-scaled
+spinor and FP16 link storage with FP32 arithmetic, FP64 reliable updates when
+the inner residual drops by delta = 0.1, FP64 reductions, 1e-10 true relative
+residual.  One step = one complete solve through the C ABI (source packing,
+the CG with every Dslash, the reliable updates, unpacking of x), inputs
+resident in HBM.  The metric is the sustained Wilson Dslash rate over the
+solve, 1320 flop per output site per parity apply, next to the plain FP64 CG
+on the same inputs and the isolated FP16 Dslash kernel against the HBM
+roofline.
+
+--impl reference times the FP64 CPU oracle (numpy) on the same workload:
+each step is one oracle parity-Dslash apply on the 32^3x64 lattice.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 64)
+KAPPA = 0.1245
+EPS = 0.25
+BC = (1.0, 1.0, 1.0, -1.0)
+DELTA = 0.1
+TOL = 1e-10
+CONFIG_ID = 2
+FLOP_PER_SITE = 1320
+WORKLOAD = "eo-mixed-fp16-cg-32x32x32x64"
+METRIC = "Wilson Dslash GFLOP/s & HBM GB/s; mixed-vs-FP64 CG time at 1e-10 residual"
+# algorithmic bytes per output site of one parity apply (FP16 storage, 12-real links):
+# 8 links x 24 B + input spinor 48 B + its FP32 scale + output 48 B + scale
+BYTES_PER_SITE_F16 = 8 * 24 + 52 + 52
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline_sample(u_np, psi_np):
+    """Oracle (numpy FP64) parity Dslash on the full lattice, timed on the host."""
+    import oracle
+
+    vh = u_np.shape[1] * u_np.shape[2] * u_np.shape[3] * u_np.shape[4] // 2
+    t0 = time.perf_counter()
+    oracle.hop_block(u_np, psi_np, BC, 0)
+    dt = time.perf_counter() - t0
+    return {"value": FLOP_PER_SITE * vh / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle parity Dslash (hop_block, numpy FP64) on 32^3x64, {dt:.1f} s"}
+
+
+def make_inputs(device):
+    import torch
+
+    import synth
+
+    u = synth.gauge_field(DIMS, EPS, synth.seed_for(CONFIG_ID, 0), device=device, as_numpy=False)
+    b = torch.from_numpy(synth.gaussian_spinor(DIMS, synth.seed_for(CONFIG_ID, 1))).to(device)
+    return u, b
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import synth
+
+    u = synth.gauge_field(DIMS, EPS, synth.seed_for(CONFIG_ID, 0))
+    psi = synth.gaussian_spinor(DIMS, synth.seed_for(CONFIG_ID, 1))
+    vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+    for _ in range(args.warmup):
+        oracle.hop_block(u, psi, BC, 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.hop_block(u, psi, BC, 0)
+    dt = time.perf_counter() - t0
+    value = FLOP_PER_SITE * vh * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA,
+                   "step": "one oracle parity Dslash apply (numpy FP64, CPU)"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle parity Dslash applies on 32^3x64"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_cola(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2302_00850_gb300 as cola
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    lx, ly, lz, lt = DIMS
+    vol = lx * ly * lz * lt
+    vh = vol // 2
+
+    u, b = make_inputs(dev)
+    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f32", "f16"), recon={"f64": 18, "f32": 12, "f16": 12})
+
+    def solve(inner="f16", bb=b, gg=g):
+        return cola.cg_solve(gg, bb, tol=TOL, op="eo", inner=inner, delta=DELTA, use_graph=True)
+
+    for _ in range(args.warmup):
+        x, info = solve()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        x, info = solve()
+        infos.append(info[0])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+
+    iters = [i.iters for i in infos]
+    rus = [i.reliable_updates for i in infos]
+    # parity Dslash applies per solve: 4 per iteration (inner precision) + 4 per FP64 residual
+    n_ds = [4 * it + 4 * ru for it, ru in zip(iters, rus)]
+    flops = sum(FLOP_PER_SITE * vh * n for n in n_ds) * world
+    value = flops / (t_ms * 1e-3) / 1e9
+    launches = sum(6 + 8 * it + 6 * ru + 4 for it, ru in zip(iters, rus))
+
+    # plain FP64 CG on the same inputs (the comparison of the metric)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    x64, info64 = solve("f64")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    mixed_ms = t_ms / args.steps
+
+    # isolated FP16 parity Dslash (dominant kernel): chained applies p -> t -> p
+    p16 = cola.pack(g, b, "f16")
+    t16 = g.empty_packed("f16")
+    for _ in range(5):
+        cola.dslash(g, t16, p16, parity=1, prec="f16")
+        cola.dslash(g, p16, t16, parity=0, prec="f16")
+    nrep = 100
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    d0.record(stream)
+    for _ in range(nrep):
+        cola.dslash(g, t16, p16, parity=1, prec="f16")
+        cola.dslash(g, p16, t16, parity=0, prec="f16")
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ds_us = d0.elapsed_time(d1) * 1e3 / (2 * nrep)
+    ds_bytes = BYTES_PER_SITE_F16 * vh
+    achieved = ds_bytes / (ds_us * 1e-6) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+
+    # isolated FP64 parity Dslash (reliable updates; FP64-ALU bound on this part)
+    p64 = cola.pack(g, b, "f64")
+    t64 = g.empty_packed("f64")
+    cola.dslash(g, t64, p64, parity=1, prec="f64")
+    torch.cuda.synchronize()
+    d0.record(stream)
+    for _ in range(10):
+        cola.dslash(g, t64, p64, parity=1, prec="f64")
+        cola.dslash(g, p64, t64, parity=0, prec="f64")
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ds64_us = d0.elapsed_time(d1) * 1e3 / 20
+
+    # end to end through the public API with host buffers
+    u_host = u.cpu().pin_memory()
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    del g
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    w0 = time.perf_counter()
+    e2e_ds = 0
+    for _ in range(e2e_steps):
+        ud = u_host.to(dev, non_blocking=True)
+        bd = b_host.to(dev, non_blocking=True)
+        ge = cola.Gauge(ud, DIMS, KAPPA, BC, precisions=("f64", "f16"), recon={"f64": 18, "f16": 12})
+        xe, ie = cola.cg_solve(ge, bd, tol=TOL, op="eo", inner="f16", delta=DELTA, use_graph=True)
+        x_host.copy_(xe, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ds += 4 * ie[0].iters + 4 * ie[0].reliable_updates
+        del ge
+    e2e_s = (time.perf_counter() - w0) / e2e_steps
+    e2e_value = FLOP_PER_SITE * vh * (e2e_ds / e2e_steps) * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(u.cpu().numpy(), b.cpu().numpy())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mixed_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16-storage/f32-math/f64-reliable", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA, "links": "exp(0.25 i H)",
+                       "inner": "f16 (per-site scale), 12-real links", "delta": DELTA, "tol": TOL,
+                       "l2": "inputs larger than L2 (FP16 links 201 MB, FP64 source 403 MB)",
+                       "parallelism": f"replicas{world}"},
+            "solve": {"iters": iters[-1], "reliable_updates": rus[-1],
+                      "true_rel_resid": infos[-1].true_rel_resid, "mixed_ms": mixed_ms},
+            "fp64_cg": {"ms": fp64_ms, "iters": info64[0].iters, "true_rel_resid": info64[0].true_rel_resid,
+                        "mixed_over_fp64_time": mixed_ms / fp64_ms},
+            "dslash_f16": {"us_per_parity_apply": ds_us, "gflops": FLOP_PER_SITE * vh / (ds_us * 1e-6) / 1e9,
+                           "algorithmic_gbs": achieved},
+            "dslash_f64": {"us_per_parity_apply": ds64_us, "gflops": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e9},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "dslash_kernel<F16,12> parity apply",
+                         "peak_kind": f"{peak_kind} hbm_gbs (burst, kernel timed alone)"},
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": u_host.numel() * 16 + b_host.numel() * 16,
+                    "d2h_bytes_per_step": x_host.numel() * 16, "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cola", choices=["cola", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cola(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * cola.h -- C ABI of the GB300 Wilson-Dirac hot path.
+ *
+ * Kamleh, "Evolving the COLA software library" (Lattice 2022) describes a
+ * GPU fermion-matrix inverter written in CUDA C/C++ and called through a
+ * plain C interface (ISO C Binding) from Fortran; this header is that kind of
+ * boundary.  The paper does not write the operator.  The library implements
+ * the kappa-normalised Wilson matrix
+ *
+ *   (H psi)(x) = sum_mu (1 - gamma_mu) Ut_mu(x) psi(x+mu)
+ *              + (1 + gamma_mu) Ut_mu(x-mu)^dag psi(x-mu),     D = 1 - kappa H,
+ *
+ * gamma matrices in the Hermitian chiral (DeGrand-Rossi) basis, Ut_mu(x) =
+ * U_mu(x) * bc[mu] on links that cross the lattice boundary (x_mu = L_mu - 1).
+ * Even-odd preconditioning uses the Schur operator on even sites,
+ * Mhat = 1 - kappa^2 H_eo H_oe, whose determinant equals det D.
+ *
+ * Conventions shared by every call:
+ *  - Site index i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
+ *    All four extents must be even and >= 2.
+ *  - Canonical spinor: complex128 [V][4 spin][3 colour], interleaved (re, im).
+ *    Canonical gauge field: complex128 [4 mu][V][3][3], row-major 3x3.
+ *    Multi-RHS canonical spinors: [nrhs][V][4][3].
+ *  - Packed spinor (the layout the Dslash reads): both parities, even first,
+ *    each parity a structure of arrays over its V/2 sites; per right-hand
+ *    side cola_spinor_bytes(lat, prec, 1) bytes, right-hand side outermost.
+ *  - Every pointer is a DEVICE pointer unless its comment says host.  The
+ *    caller owns every buffer it passes; the library owns only what a handle
+ *    holds (packed links, solver workspace), released by cola_gauge_destroy.
+ *  - All work is ordered on the given stream; calls return after enqueuing,
+ *    except cola_cg_solve*, which synchronise the stream once at the end to
+ *    fill their info structs.
+ *  - Errors are returned as cola_status codes; nothing aborts.  The message
+ *    of the last failure on the calling thread is cola_last_error().
+ */
+#ifndef COLA_H
+#define COLA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t; /* identical to CUDA's own typedef */
+
+typedef enum {
+    COLA_OK = 0,
+    COLA_ERR_ARG = -1,           /* invalid argument: null pointer, odd extent, bad enum, size */
+    COLA_ERR_CUDA = -2,          /* a CUDA runtime call failed (message has the CUDA error) */
+    COLA_ERR_NOMEM = -3,         /* device allocation failed */
+    COLA_ERR_NOT_CONVERGED = -4, /* max_iter reached; x holds the best iterate */
+    COLA_ERR_BREAKDOWN = -5,     /* non-finite or non-positive CG scalar (e.g. NaN source) */
+    COLA_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+    COLA_ERR_UNSUPPORTED = -7    /* precision not packed in this gauge handle */
+} cola_status;
+
+typedef enum { COLA_F64 = 0, COLA_F32 = 1, COLA_F16 = 2 } cola_prec;
+
+enum { COLA_OP_FULL = 0, COLA_OP_EO = 1 };
+enum { COLA_SYS_NORMAL = 0, COLA_SYS_DIRAC = 1 };
+enum { COLA_PARITY_EVEN = 0, COLA_PARITY_ODD = 1, COLA_PARITY_BOTH = 2 };
+
+/* Lattice and operator parameters.  bc[mu] = (re, im) of the phase on links
+ * crossing the boundary in direction mu: (1,0) periodic, (-1,0) anti-periodic. */
+typedef struct {
+    int dims[4];     /* Lx, Ly, Lz, Lt */
+    double kappa;    /* hopping parameter */
+    double bc[4][2];
+} cola_lattice;
+
+/* Which packed copies of the links a handle holds.  prec_mask bit (1 << p)
+ * requests precision p; recon[p] is 12 (rows 0-1 stored, row 2 rebuilt as
+ * conj(row0 x row1)) or 18 (all rows stored).  FP16 links are SU(3) entries,
+ * |u_ij| <= 1, so they are stored without a scale factor. */
+typedef struct {
+    unsigned prec_mask;
+    int recon[3];
+} cola_gauge_opts;
+
+typedef struct cola_gauge_s *cola_gauge;
+
+/* Pack the canonical FP64 links (device, [4][V][3][3] complex128, caller-owned,
+ * read during the call's stream work only) into every requested precision.
+ * The links must be SU(3) for recon 12.  On success *out owns device memory. */
+cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev,
+                              const cola_gauge_opts *opts, cudaStream_t stream,
+                              cola_gauge *out);
+cola_status cola_gauge_destroy(cola_gauge g);
+
+/* Bytes of one packed spinor field (both parities) times nrhs. */
+size_t cola_spinor_bytes(const cola_lattice *lat, cola_prec prec, int nrhs);
+
+/* canonical complex128 [nrhs][V][4][3] <-> packed.  FP16 stores each site as
+ * half values scaled by that site's max |component| (an FP32 scale). */
+cola_status cola_spinor_pack(cola_gauge g, void *packed_dev, const void *canon_dev,
+                             cola_prec prec, int nrhs, cudaStream_t stream);
+cola_status cola_spinor_unpack(cola_gauge g, void *canon_dev, const void *packed_dev,
+                               cola_prec prec, int nrhs, cudaStream_t stream);
+
+/* Hopping term on packed fields, for each of nrhs right-hand sides:
+ *   out_p = a * in_self_p + b * H_{p,1-p} in_{1-p}
+ * for p = parity (0 even, 1 odd) or both parities (2).  dagger != 0 applies
+ * H^dag (projectors swapped).  in_self may be NULL when a == 0.  out must not
+ * alias in.  FP64 accumulates in double, FP32/FP16 storage in float. */
+cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const void *in_self,
+                              double a, double b, int parity, int dagger, cola_prec prec,
+                              int nrhs, cudaStream_t stream);
+
+/* out = M^dag M in on packed fields.  op COLA_OP_FULL: M = D on the whole
+ * lattice.  op COLA_OP_EO: M = Mhat on the even half (the odd half of out is
+ * left as it was).  Uses workspace held by the handle (allocated on first use). */
+cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
+                             int nrhs, cudaStream_t stream);
+
+typedef struct {
+    double tol;      /* target true relative residual (e.g. 1e-10) */
+    int max_iter;    /* iteration cap (CG steps) */
+    int op;          /* COLA_OP_FULL or COLA_OP_EO */
+    int system;      /* COLA_SYS_NORMAL: M^dag M x = b;  COLA_SYS_DIRAC: D x = b */
+    int inner;       /* cola_prec of the inner iterations; COLA_F64 = plain FP64 CG */
+    double delta;    /* reliable-update trigger: |r_inner| < delta * |r| at last update */
+    int nrhs;        /* right-hand sides solved together (1..64) */
+    int use_graph;   /* 1: run the iteration loop as one CUDA graph with device-side control */
+} cola_solver_params;
+
+typedef struct {
+    int iters;             /* CG iterations */
+    int reliable_updates;  /* FP64 residual recomputations, the initial one included */
+    double true_rel_resid; /* |b - A x| / |b| recomputed in FP64 at the end */
+    double seconds;        /* wall time of the call */
+    int status;            /* cola_status of this right-hand side */
+} cola_solve_info;
+
+/* Solve for x in canonical FP64 layout ([nrhs][V][4][3] complex128, device).
+ * On entry x holds the initial guess (zeros for a cold start); on return the
+ * solution.  SYS_NORMAL + OP_FULL: D^dag D x = b.  SYS_NORMAL + OP_EO:
+ * Mhat^dag Mhat x_e = b_e (odd sites of b ignored, of x set to zero).
+ * SYS_DIRAC: D x = b (OP_EO through the Schur complement and its normal
+ * equations, x_o = b_o + kappa H_oe x_e).  info has nrhs entries (host). */
+cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev,
+                          const cola_solver_params *params, cola_solve_info *info,
+                          cudaStream_t stream);
+
+/* Fermion force of S = phi^dag (D^dag D)^-1 phi given X = (D^dag D)^-1 phi and
+ * Y = D X (canonical FP64, device).  Output force_dev: real FP64 [4][V][8],
+ * F^a_mu(x) = dS/d eps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x), T^a = lambda^a/2:
+ * F^a = -2 kappa Im Tr[T^a Ut_mu(x) (P + Q^dag)], with
+ * P_ba = sum_s [(1-gamma_mu) X(x+mu)]_sb conj(Y(x)_sa),
+ * Q_ba = sum_s [(1+gamma_mu) X(x)]_sb conj(Y(x+mu)_sa).  Accumulated in FP64. */
+cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_dev,
+                               const void *Y_dev, cudaStream_t stream);
+
+/* Raw complex link gradient of a real loss through y = D psi, in the
+ * convention grad = 2 dL/d conj(U) (PyTorch's), given g = that gradient on y:
+ * grad_U_mu(x)_ab = -kappa conj(ph) [ sum_s g(x)_sa conj([(1-gamma_mu) psi(x+mu)]_sb)
+ *                                    + sum_s [(1+gamma_mu) psi(x)]_sa conj(g(x+mu)_sb) ],
+ * ph the link's boundary phase.  Canonical FP64 in and out ([4][V][3][3]). */
+cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev,
+                                 const void *gy_dev, cudaStream_t stream);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char *cola_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLA_H */

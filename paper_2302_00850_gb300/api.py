@@ -1,0 +1,192 @@
+"""Python API over the C ABI (include/cola.h), on torch CUDA tensors.
+
+torch supplies device memory, the current stream and autograd plumbing; every
+step of the Wilson-Dirac path (packing, hopping term, solver, force) runs in
+libcola's CUDA kernels.  There is no CPU implementation here and no fallback:
+calls on tensors that are not CUDA tensors raise.
+
+Canonical layouts (complex128, x fastest):
+  spinor  [Lt, Lz, Ly, Lx, 4, 3], or [nrhs, Lt, Lz, Ly, Lx, 4, 3]
+  links   [4, Lt, Lz, Ly, Lx, 3, 3]
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import F16, F32, F64, OP_EO, OP_FULL, SYS_DIRAC, SYS_NORMAL, ColaError, check  # noqa: F401
+
+PREC = {"f64": F64, "f32": F32, "f16": F16, F64: F64, F32: F32, F16: F16}
+OPS = {"full": OP_FULL, "eo": OP_EO, OP_FULL: OP_FULL, OP_EO: OP_EO}
+SYSTEMS = {"normal": SYS_NORMAL, "dirac": SYS_DIRAC, SYS_NORMAL: SYS_NORMAL, SYS_DIRAC: SYS_DIRAC}
+
+
+def _stream(device=None) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("libcola takes CUDA tensors (no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("libcola takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _complex_field(t: torch.Tensor, numel: int, what: str):
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{what} must be complex128")
+    if t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {numel}")
+    return _ptr(t)
+
+
+class Gauge:
+    """Packed links of one lattice (a cola_gauge handle).
+
+    links: complex128 CUDA tensor [4, Lt, Lz, Ly, Lx, 3, 3] (SU(3) for recon 12)
+    dims: (Lx, Ly, Lz, Lt); bc: per-direction boundary phase (complex)
+    precisions: any of "f64", "f32", "f16"; recon: dict precision -> 12 or 18
+    """
+
+    def __init__(self, links, dims, kappa, bc=(1, 1, 1, -1), precisions=("f64", "f32", "f16"), recon=None):
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        self.bc = tuple(complex(b) for b in bc)
+        lx, ly, lz, lt = self.dims
+        self.volume = lx * ly * lz * lt
+        self.lat = _lib.Lattice()
+        for m in range(4):
+            self.lat.dims[m] = self.dims[m]
+            self.lat.bc[m][0] = self.bc[m].real
+            self.lat.bc[m][1] = self.bc[m].imag
+        self.lat.kappa = self.kappa
+        recon = dict(recon or {})
+        self.recon = {}
+        opts = _lib.GaugeOpts()
+        opts.prec_mask = 0
+        for p in precisions:
+            pi = PREC[p]
+            opts.prec_mask |= 1 << pi
+            r = int(recon.get(p, recon.get(pi, 18 if pi == F64 else 12)))
+            opts.recon[pi] = r
+            self.recon[pi] = r
+        self.precisions = {PREC[p] for p in precisions}
+        self.device = links.device
+        self.handle = ctypes.c_void_p()
+        check(self.lib.cola_gauge_create(ctypes.byref(self.lat), _complex_field(links, 4 * self.volume * 9, "links"),
+                                         ctypes.byref(opts), _stream(self.device), ctypes.byref(self.handle)))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.cola_gauge_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spinor_shape(self, nrhs=None):
+        lx, ly, lz, lt = self.dims
+        base = (lt, lz, ly, lx, 4, 3)
+        return base if nrhs is None else (nrhs,) + base
+
+    def spinor_bytes(self, prec, nrhs=1) -> int:
+        return int(self.lib.cola_spinor_bytes(ctypes.byref(self.lat), PREC[prec], int(nrhs)))
+
+    def empty_packed(self, prec, nrhs=1) -> torch.Tensor:
+        return torch.empty(self.spinor_bytes(prec, nrhs), dtype=torch.uint8, device=self.device)
+
+
+def _nrhs_of(g: Gauge, psi: torch.Tensor):
+    n = psi.numel() // (g.volume * 12)
+    if n * g.volume * 12 != psi.numel():
+        raise ValueError("spinor size is not a multiple of V * 12")
+    return n
+
+
+def pack(g: Gauge, psi: torch.Tensor, prec="f64") -> torch.Tensor:
+    """Canonical complex128 spinor(s) -> packed field in precision `prec`."""
+    nrhs = _nrhs_of(g, psi)
+    out = g.empty_packed(prec, nrhs)
+    check(g.lib.cola_spinor_pack(g.handle, _ptr(out), _ptr(psi), PREC[prec], nrhs, _stream(g.device)))
+    return out
+
+
+def unpack(g: Gauge, packed: torch.Tensor, prec="f64", nrhs=None) -> torch.Tensor:
+    n = 1 if nrhs is None else nrhs
+    out = torch.empty(g.spinor_shape(nrhs), dtype=torch.complex128, device=g.device)
+    check(g.lib.cola_spinor_unpack(g.handle, _ptr(out), _ptr(packed), PREC[prec], n, _stream(g.device)))
+    return out
+
+
+def dslash(g: Gauge, out, inp, in_self=None, a=0.0, b=1.0, parity=2, dagger=False, prec="f64", nrhs=1):
+    """out_p = a in_self_p + b H_{p,1-p} in_{1-p} on packed fields (parity 0, 1 or 2 = both)."""
+    check(g.lib.cola_dslash_apply(g.handle, _ptr(out), _ptr(inp), _ptr(in_self) if in_self is not None else None,
+                                  float(a), float(b), int(parity), int(bool(dagger)), PREC[prec], int(nrhs),
+                                  _stream(g.device)))
+    return out
+
+
+def mdagm(g: Gauge, out, inp, op="eo", prec="f64", nrhs=1):
+    """out = M^dag M in on packed fields (op "eo": Mhat on the even half; "full": D)."""
+    check(g.lib.cola_mdagm_apply(g.handle, _ptr(out), _ptr(inp), OPS[op], PREC[prec], int(nrhs), _stream(g.device)))
+    return out
+
+
+def apply_dirac(g: Gauge, psi: torch.Tensor, dagger=False, prec="f64") -> torch.Tensor:
+    """D psi (or D^dag psi) on canonical complex128 fields, through the packed kernels."""
+    nrhs = _nrhs_of(g, psi)
+    pin = pack(g, psi, prec)
+    pout = g.empty_packed(prec, nrhs)
+    dslash(g, pout, pin, pin, a=1.0, b=-g.kappa, parity=2, dagger=dagger, prec=prec, nrhs=nrhs)
+    return unpack(g, pout, prec, None if psi.dim() == 6 else nrhs).reshape(psi.shape)
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    reliable_updates: int
+    true_rel_resid: float
+    seconds: float
+    status: int
+
+
+def cg_solve(g: Gauge, b: torch.Tensor, x0: torch.Tensor | None = None, tol=1e-10, max_iter=100000, op="eo",
+             system="normal", inner="f64", delta=0.1, use_graph=False, raise_on_error=True):
+    """Solve with CG (see cola_cg_solve).  Returns (x, [SolveInfo per right-hand side])."""
+    nrhs = _nrhs_of(g, b)
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    prm = _lib.SolverParams(float(tol), int(max_iter), OPS[op], SYSTEMS[system], PREC[inner], float(delta), nrhs,
+                            int(bool(use_graph)))
+    infos = (_lib.SolveInfo * nrhs)()
+    st = g.lib.cola_cg_solve(g.handle, _ptr(x), _complex_field(b, nrhs * g.volume * 12, "b"), ctypes.byref(prm),
+                             infos, _stream(g.device))
+    res = [SolveInfo(i.iters, i.reliable_updates, i.true_rel_resid, i.seconds, i.status) for i in infos]
+    if st != 0 and (raise_on_error or st not in (-4, -5)):
+        check(st)
+    return x, res
+
+
+def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
+    """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X."""
+    lx, ly, lz, lt = g.dims
+    out = torch.empty((4, lt, lz, ly, lx, 8), dtype=torch.float64, device=g.device)
+    check(g.lib.cola_fermion_force(g.handle, _ptr(out), _complex_field(X, g.volume * 12, "X"),
+                                   _complex_field(Y, g.volume * 12, "Y"), _stream(g.device)))
+    return out
+
+
+def dirac_link_grad(g: Gauge, psi: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
+    """Raw complex link gradient (torch convention) of a real loss through y = D psi, given dL/dy."""
+    lx, ly, lz, lt = g.dims
+    out = torch.empty((4, lt, lz, ly, lx, 3, 3), dtype=torch.complex128, device=g.device)
+    check(g.lib.cola_dirac_link_grad(g.handle, _ptr(out), _complex_field(psi, g.volume * 12, "psi"),
+                                     _complex_field(gy, g.volume * 12, "gy"), _stream(g.device)))
+    return out

@@ -1,0 +1,320 @@
+// C ABI entry points: argument checks, gauge handles, workspace, and the
+// operator compositions (D, Mhat, their normal operators) built from the
+// hopping kernel.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cola_impl.h"
+
+namespace cola {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+cola_status cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return COLA_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? COLA_ERR_NOMEM : COLA_ERR_CUDA;
+}
+
+#define COLA_TRY(expr)                       \
+    do {                                     \
+        cola_status _st = (expr);            \
+        if (_st != COLA_OK) return _st;      \
+    } while (0)
+#define COLA_CUDA(expr, what) COLA_TRY(cuda_check((expr), what))
+
+static cola_status arg_error(const std::string &msg) {
+    set_error(msg);
+    return COLA_ERR_ARG;
+}
+
+static cola_status check_lattice(const cola_lattice *lat) {
+    if (!lat) return arg_error("lattice is null");
+    long long v = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (lat->dims[m] < 2 || lat->dims[m] % 2)
+            return arg_error("lattice extents must be even and >= 2 (dims[" + std::to_string(m) +
+                             "] = " + std::to_string(lat->dims[m]) + ")");
+        v *= lat->dims[m];
+    }
+    if (v > (1ll << 30)) return arg_error("lattice volume above 2^30 sites");
+    if (!std::isfinite(lat->kappa)) return arg_error("kappa is not finite");
+    for (int m = 0; m < 4; ++m)
+        if (!std::isfinite(lat->bc[m][0]) || !std::isfinite(lat->bc[m][1]))
+            return arg_error("boundary phase is not finite");
+    return COLA_OK;
+}
+
+static Geom make_geom(const cola_lattice &lat) {
+    Geom g;
+    for (int m = 0; m < 4; ++m) g.L[m] = lat.dims[m];
+    g.Lxh = g.L[0] / 2;
+    g.V = g.L[0] * g.L[1] * g.L[2] * g.L[3];
+    g.Vh = g.V / 2;
+    g.stride[0] = 1;
+    g.stride[1] = g.Lxh;
+    g.stride[2] = g.Lxh * g.L[1];
+    g.stride[3] = g.Lxh * g.L[1] * g.L[2];
+    for (int m = 0; m < 4; ++m) {
+        g.bc[m][0] = lat.bc[m][0];
+        g.bc[m][1] = lat.bc[m][1];
+        g.bc_trivial[m] = (lat.bc[m][0] == 1.0 && lat.bc[m][1] == 0.0);
+    }
+    return g;
+}
+
+static cola_status check_prec(cola_gauge g, int prec) {
+    if (prec < 0 || prec > 2) return arg_error("precision must be COLA_F64, COLA_F32 or COLA_F16");
+    if (!g->links[prec]) {
+        set_error("gauge handle holds no links of precision " + std::to_string(prec));
+        return COLA_ERR_UNSUPPORTED;
+    }
+    return COLA_OK;
+}
+
+cola_status ws_slot(cola_gauge g, int k, size_t bytes, void **out) {
+    if (g->slot_bytes[k] < bytes) {
+        if (g->slot[k]) cudaFree(g->slot[k]);
+        g->slot[k] = nullptr;
+        g->slot_bytes[k] = 0;
+        COLA_CUDA(cudaMalloc(&g->slot[k], bytes), "workspace allocation");
+        g->slot_bytes[k] = bytes;
+    }
+    *out = g->slot[k];
+    return COLA_OK;
+}
+
+cola_status ws_reduce(cola_gauge g, size_t nrows, size_t nblocks) {
+    const size_t need = nrows * nblocks;
+    if (g->partials_count < need) {
+        if (g->partials) cudaFree(g->partials);
+        g->partials = nullptr;
+        g->partials_count = 0;
+        COLA_CUDA(cudaMalloc(&g->partials, need * sizeof(double)), "reduction scratch");
+        g->partials_count = need;
+    }
+    if (g->counters_count < nrows) {
+        if (g->counters) cudaFree(g->counters);
+        g->counters = nullptr;
+        g->counters_count = 0;
+        COLA_CUDA(cudaMalloc(&g->counters, nrows * sizeof(unsigned)), "reduction counters");
+        COLA_CUDA(cudaMemset(g->counters, 0, nrows * sizeof(unsigned)), "reduction counters");
+        g->counters_count = nrows;
+    }
+    return COLA_OK;
+}
+
+cola_status ws_states(cola_gauge g, int n) {
+    if (g->states_count < n) {
+        if (g->states) cudaFree(g->states);
+        if (g->h_states) cudaFreeHost(g->h_states);
+        g->states = nullptr;
+        g->h_states = nullptr;
+        g->states_count = 0;
+        COLA_CUDA(cudaMalloc(&g->states, n * sizeof(CgState)), "solver state");
+        COLA_CUDA(cudaMallocHost(&g->h_states, n * sizeof(CgState)), "solver state (host)");
+        g->states_count = n;
+    }
+    return COLA_OK;
+}
+
+static int rhs_per_block_for(int nrhs) {
+    if (nrhs <= 1) return 1;
+    if (nrhs <= 4) return nrhs;
+    return 4;
+}
+
+DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
+                            int parity0, double a, double b) {
+    DslashArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.g = g->geom;
+    A.out = out;
+    A.in = in;
+    A.xin = xin;
+    A.links = g->links[prec];
+    A.link_parity_stride = g->link_parity_bytes[prec];
+    A.link_dir_stride = link_dir_bytes(prec, g->recon[prec], g->geom.Vh);
+    A.parity_stride = spinor_parity_bytes(prec, g->geom.Vh);
+    A.rhs_stride = 2 * A.parity_stride;
+    A.parity0 = parity0;
+    A.nrhs = nrhs;
+    A.rhs_per_block = rhs_per_block_for(nrhs);
+    A.a = a;
+    A.b = b;
+    return A;
+}
+
+static cola_status dslash_launch(cola_gauge g, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
+                                 bool red, cudaStream_t s) {
+    if (red) {
+        const int bx = default_dslash_block(prec, A.rhs_per_block);
+        const size_t nblocks = (size_t)((g->geom.Vh + bx - 1) / bx) * nparity;
+        const size_t ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
+        COLA_TRY(ws_reduce(g, A.nrhs > (int)ngroups ? A.nrhs : ngroups, nblocks));
+        A.partials = g->partials;
+        A.counters = g->counters;
+    }
+    return cuda_check(launch_dslash(prec, g->recon[prec], A, nparity, dagger, xpay, red, 0, s), "dslash launch");
+}
+
+cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
+                        CgState *st, bool filter_ru, bool reduce, cudaStream_t s) {
+    const double k = g->lat.kappa;
+    if (op == COLA_OP_EO) {
+        DslashArgs A = make_dslash_args(g, prec, t, in, nullptr, nrhs, 1, 0.0, 1.0);
+        A.state = st;
+        A.filter_ru = filter_ru;
+        COLA_TRY(dslash_launch(g, prec, A, 1, false, false, false, s));
+        A = make_dslash_args(g, prec, mp, t, in, nrhs, 0, 1.0, -k * k);
+        A.state = st;
+        A.filter_ru = filter_ru;
+        COLA_TRY(dslash_launch(g, prec, A, 1, false, true, reduce, s));
+        A = make_dslash_args(g, prec, t, mp, nullptr, nrhs, 1, 0.0, 1.0);
+        A.state = st;
+        A.filter_ru = filter_ru;
+        COLA_TRY(dslash_launch(g, prec, A, 1, true, false, false, s));
+        A = make_dslash_args(g, prec, out, t, mp, nrhs, 0, 1.0, -k * k);
+        A.state = st;
+        A.filter_ru = filter_ru;
+        return dslash_launch(g, prec, A, 1, true, true, false, s);
+    }
+    DslashArgs A = make_dslash_args(g, prec, mp, in, in, nrhs, 0, 1.0, -k);
+    A.state = st;
+    A.filter_ru = filter_ru;
+    COLA_TRY(dslash_launch(g, prec, A, 2, false, true, reduce, s));
+    A = make_dslash_args(g, prec, out, mp, mp, nrhs, 0, 1.0, -k);
+    A.state = st;
+    A.filter_ru = filter_ru;
+    return dslash_launch(g, prec, A, 2, true, true, false, s);
+}
+
+}  // namespace cola
+
+using namespace cola;
+
+extern "C" {
+
+const char *cola_last_error(void) { return g_last_error.c_str(); }
+
+size_t cola_spinor_bytes(const cola_lattice *lat, cola_prec prec, int nrhs) {
+    if (check_lattice(lat) != COLA_OK || prec < 0 || prec > 2 || nrhs < 1) return 0;
+    const size_t vh = (size_t)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3] / 2;
+    return 2 * spinor_parity_bytes(prec, (int)vh) * (size_t)nrhs;
+}
+
+cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev, const cola_gauge_opts *opts,
+                              cudaStream_t stream, cola_gauge *out) {
+    COLA_TRY(check_lattice(lat));
+    if (!links_dev || !opts || !out) return arg_error("null argument to cola_gauge_create");
+    if ((opts->prec_mask & 7u) == 0 || (opts->prec_mask & ~7u))
+        return arg_error("prec_mask must request at least one of F64/F32/F16 and nothing else");
+    for (int p = 0; p < 3; ++p)
+        if ((opts->prec_mask >> p) & 1)
+            if (opts->recon[p] != 12 && opts->recon[p] != 18) return arg_error("recon must be 12 or 18");
+    *out = nullptr;
+    cola_gauge g = new cola_gauge_s();
+    g->lat = *lat;
+    g->geom = make_geom(*lat);
+    cudaGetDevice(&g->device);
+    for (int p = 0; p < 3; ++p) {
+        if (!((opts->prec_mask >> p) & 1)) continue;
+        g->recon[p] = opts->recon[p];
+        g->link_parity_bytes[p] = 4 * link_dir_bytes(p, g->recon[p], g->geom.Vh);
+        cola_status st = cuda_check(cudaMalloc(&g->links[p], 2 * g->link_parity_bytes[p]), "link allocation");
+        if (st == COLA_OK) st = cuda_check(launch_pack_gauge(p, g->recon[p], g->geom, g->links[p], links_dev, stream),
+                                           "link packing");
+        if (st != COLA_OK) {
+            cola_gauge_destroy(g);
+            return st;
+        }
+    }
+    *out = g;
+    return COLA_OK;
+}
+
+cola_status cola_gauge_destroy(cola_gauge g) {
+    if (!g) return COLA_OK;
+    cudaDeviceSynchronize();
+    for (int p = 0; p < 3; ++p)
+        if (g->links[p]) cudaFree(g->links[p]);
+    for (int k = 0; k < cola_gauge_s::kSlots; ++k)
+        if (g->slot[k]) cudaFree(g->slot[k]);
+    if (g->partials) cudaFree(g->partials);
+    if (g->counters) cudaFree(g->counters);
+    if (g->states) cudaFree(g->states);
+    if (g->h_states) cudaFreeHost(g->h_states);
+    delete g;
+    return COLA_OK;
+}
+
+static cola_status check_rhs(int nrhs) {
+    if (nrhs < 1 || nrhs > 65535) return arg_error("nrhs must be in 1..65535");
+    return COLA_OK;
+}
+
+cola_status cola_spinor_pack(cola_gauge g, void *packed_dev, const void *canon_dev, cola_prec prec, int nrhs,
+                             cudaStream_t stream) {
+    if (!g || !packed_dev || !canon_dev) return arg_error("null argument to cola_spinor_pack");
+    if (prec < 0 || prec > 2) return arg_error("bad precision");
+    COLA_TRY(check_rhs(nrhs));
+    return cuda_check(launch_pack_spinor(prec, g->geom, packed_dev, canon_dev, nrhs, 3, stream), "spinor packing");
+}
+
+cola_status cola_spinor_unpack(cola_gauge g, void *canon_dev, const void *packed_dev, cola_prec prec, int nrhs,
+                               cudaStream_t stream) {
+    if (!g || !packed_dev || !canon_dev) return arg_error("null argument to cola_spinor_unpack");
+    if (prec < 0 || prec > 2) return arg_error("bad precision");
+    COLA_TRY(check_rhs(nrhs));
+    return cuda_check(launch_unpack_spinor(prec, g->geom, canon_dev, packed_dev, nrhs, 3, stream),
+                      "spinor unpacking");
+}
+
+cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const void *in_self, double a, double b,
+                              int parity, int dagger, cola_prec prec, int nrhs, cudaStream_t stream) {
+    if (!g || !out || !in) return arg_error("null argument to cola_dslash_apply");
+    if (parity < 0 || parity > 2) return arg_error("parity must be 0, 1 or 2");
+    if (a != 0.0 && !in_self) return arg_error("in_self is null but a != 0");
+    if (out == in) return arg_error("out must not alias in");
+    COLA_TRY(check_prec(g, prec));
+    COLA_TRY(check_rhs(nrhs));
+    const bool xpay = a != 0.0;
+    DslashArgs A = make_dslash_args(g, prec, out, in, xpay ? in_self : nullptr, nrhs, parity == 2 ? 0 : parity, a, b);
+    return dslash_launch(g, prec, A, parity == 2 ? 2 : 1, dagger != 0, xpay, false, stream);
+}
+
+cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec, int nrhs,
+                             cudaStream_t stream) {
+    if (!g || !out || !in) return arg_error("null argument to cola_mdagm_apply");
+    if (op != COLA_OP_FULL && op != COLA_OP_EO) return arg_error("op must be COLA_OP_FULL or COLA_OP_EO");
+    if (out == in) return arg_error("out must not alias in");
+    COLA_TRY(check_prec(g, prec));
+    COLA_TRY(check_rhs(nrhs));
+    const size_t bytes = 2 * spinor_parity_bytes(prec, g->geom.Vh) * (size_t)nrhs;
+    void *t, *mp;
+    COLA_TRY(ws_slot(g, 0, bytes, &t));
+    COLA_TRY(ws_slot(g, 1, bytes, &mp));
+    return apply_mdagm(g, prec, op, out, in, t, mp, nrhs, nullptr, false, false, stream);
+}
+
+cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_dev, const void *Y_dev,
+                               cudaStream_t stream) {
+    if (!g || !force_dev || !X_dev || !Y_dev) return arg_error("null argument to cola_fermion_force");
+    COLA_TRY(check_prec(g, COLA_F64));
+    return cuda_check(launch_force(g->geom, g->lat.kappa, g->links[COLA_F64], g->recon[COLA_F64], force_dev, X_dev,
+                                   Y_dev, stream),
+                      "force launch");
+}
+
+cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev, const void *gy_dev,
+                                 cudaStream_t stream) {
+    if (!g || !grad_links_dev || !psi_dev || !gy_dev) return arg_error("null argument to cola_dirac_link_grad");
+    return cuda_check(launch_link_grad(g->geom, g->lat.kappa, grad_links_dev, psi_dev, gy_dev, stream),
+                      "link gradient launch");
+}
+
+}  // extern "C"

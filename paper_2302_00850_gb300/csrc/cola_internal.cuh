@@ -1,0 +1,401 @@
+// Internal device-side building blocks: lattice geometry, packed field
+// accessors, complex arithmetic, SU(3) link reconstruction and block
+// reductions.  Shared by every kernel translation unit of libcola.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/cola.h"
+
+namespace cola {
+
+// ---------------------------------------------------------------- geometry --
+// Per-lattice constants passed by value to every kernel.
+struct Geom {
+    int L[4];        // Lx, Ly, Lz, Lt
+    int Lxh;         // Lx / 2
+    int Vh;          // sites of one parity
+    int V;
+    int stride[4];   // checkerboard-index offset of a +1 step in y, z, t (x unused)
+    double bc[4][2]; // boundary phase per direction
+    int bc_trivial[4];
+};
+
+// Site coordinates of checkerboard index cb on parity `par`.
+struct Coord {
+    int x, y, z, t;
+};
+
+__device__ __forceinline__ Coord cb_coord(const Geom &g, int cb, int par) {
+    Coord c;
+    int xh = cb % g.Lxh;
+    int r = cb / g.Lxh;
+    c.y = r % g.L[1];
+    r /= g.L[1];
+    c.z = r % g.L[2];
+    c.t = r / g.L[2];
+    c.x = 2 * xh + ((par + c.y + c.z + c.t) & 1);
+    return c;
+}
+
+// Checkerboard index of the neighbour of site (c, cb) one step in direction mu
+// (dir = +1 forward, -1 backward).  The neighbour has the opposite parity.
+template <int MU, int DIR>
+__device__ __forceinline__ int nbr_cb(const Geom &g, const Coord &c, int cb) {
+    if constexpr (MU == 0) {
+        int xn = c.x + DIR;
+        if (DIR > 0 && xn == g.L[0]) xn = 0;
+        if (DIR < 0 && xn < 0) xn = g.L[0] - 1;
+        return cb - (c.x >> 1) + (xn >> 1);
+    } else {
+        const int coord = (MU == 1) ? c.y : (MU == 2) ? c.z : c.t;
+        const int L = g.L[MU];
+        const int s = g.stride[MU];
+        if (DIR > 0) return (coord == L - 1) ? cb - (L - 1) * s : cb + s;
+        return (coord == 0) ? cb + (L - 1) * s : cb - s;
+    }
+}
+
+template <int MU>
+__device__ __forceinline__ int coord_of(const Coord &c) {
+    return MU == 0 ? c.x : MU == 1 ? c.y : MU == 2 ? c.z : c.t;
+}
+
+// ----------------------------------------------------------------- complex --
+template <typename R>
+struct Cx {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
+    return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cmac(Cx<R> &acc, Cx<R> a, Cx<R> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R>
+__device__ __forceinline__ void cmac_conj(Cx<R> &acc, Cx<R> a, Cx<R> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// ------------------------------------------------------- precision traits --
+template <int P>
+struct Prec;
+template <>
+struct Prec<COLA_F64> {
+    using real = double;
+    static constexpr size_t site_bytes = 192;  // 24 doubles
+    static constexpr int link_cplx_per_group = 1;
+};
+template <>
+struct Prec<COLA_F32> {
+    using real = float;
+    static constexpr size_t site_bytes = 96;  // 24 floats
+    static constexpr int link_cplx_per_group = 2;
+};
+template <>
+struct Prec<COLA_F16> {
+    using real = float;
+    static constexpr size_t site_bytes = 52;  // 24 halves + FP32 scale
+    static constexpr int link_cplx_per_group = 2;
+};
+
+__host__ __device__ constexpr size_t spinor_parity_bytes(int prec, int vh) {
+    return (size_t)vh * (prec == COLA_F64 ? 192 : prec == COLA_F32 ? 96 : 52);
+}
+
+// Number of storage groups of one link (3x3 or its first two rows).
+__host__ __device__ constexpr int link_groups(int prec, int recon) {
+    return prec == COLA_F64 ? (recon == 12 ? 6 : 9) : (recon == 12 ? 3 : 5);
+}
+__host__ __device__ constexpr size_t link_group_bytes(int prec) {
+    return prec == COLA_F64 ? 16 : prec == COLA_F32 ? 16 : 8;
+}
+// Bytes of one direction of one parity of the packed links.
+__host__ __device__ constexpr size_t link_dir_bytes(int prec, int recon, int vh) {
+    return (size_t)link_groups(prec, recon) * link_group_bytes(prec) * vh;
+}
+
+// --------------------------------------------------------- spinor access --
+// A parity field: pointer to the first byte of one parity of one RHS.
+// Layout per precision (Vh sites, cb fastest):
+//   F64: 12 arrays of double2 (complex c = 3*spin + colour)
+//   F32:  6 arrays of float4  (complexes 2k, 2k+1)
+//   F16:  3 arrays of uint4   (8 halves = complexes 4k..4k+3, scaled),
+//         then Vh floats (per-site scale)
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<COLA_F64> {
+    __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<double> (&s)[12]) {
+        const double2 *p = reinterpret_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = __ldg(p + (size_t)c * vh + cb);
+            s[c] = {v.x, v.y};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int vh, int cb, const Cx<double> (&s)[12]) {
+        double2 *p = reinterpret_cast<double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[(size_t)c * vh + cb] = make_double2(s[c].re, s[c].im);
+    }
+};
+
+template <>
+struct SpinorIO<COLA_F32> {
+    __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
+        const float4 *p = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 v = __ldg(p + (size_t)k * vh + cb);
+            s[2 * k] = {v.x, v.y};
+            s[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int vh, int cb, const Cx<float> (&s)[12]) {
+        float4 *p = reinterpret_cast<float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            p[(size_t)k * vh + cb] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+    }
+};
+
+__device__ __forceinline__ float2 h2f(uint32_t w) {
+    __half2 h = *reinterpret_cast<__half2 *>(&w);
+    return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <>
+struct SpinorIO<COLA_F16> {
+    __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(base);
+        const float sc = __ldg(reinterpret_cast<const float *>(p + (size_t)3 * vh) + cb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = __ldg(p + (size_t)k * vh + cb);
+            float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+            s[4 * k + 0] = {a.x * sc, a.y * sc};
+            s[4 * k + 1] = {b.x * sc, b.y * sc};
+            s[4 * k + 2] = {c.x * sc, c.y * sc};
+            s[4 * k + 3] = {d.x * sc, d.y * sc};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, int vh, int cb, const Cx<float> (&s)[12]) {
+        uint4 *p = reinterpret_cast<uint4 *>(base);
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v;
+            v.x = f2h(s[4 * k + 0].re * inv, s[4 * k + 0].im * inv);
+            v.y = f2h(s[4 * k + 1].re * inv, s[4 * k + 1].im * inv);
+            v.z = f2h(s[4 * k + 2].re * inv, s[4 * k + 2].im * inv);
+            v.w = f2h(s[4 * k + 3].re * inv, s[4 * k + 3].im * inv);
+            p[(size_t)k * vh + cb] = v;
+        }
+        reinterpret_cast<float *>(p + (size_t)3 * vh)[cb] = m;
+    }
+};
+
+// ----------------------------------------------------------- link access --
+// One direction of one parity of the packed links: link_groups() arrays over
+// Vh sites.  F64 groups are one complex (double2); F32 groups two complexes
+// (float4); F16 groups two complexes (4 halves, 8 bytes).  Entries are
+// row-major u00 u01 u02 u10 ...; with recon 18 the last group of F32/F16 is
+// half padding.
+template <int P, int RECON>
+struct LinkIO;
+
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(Cx<R> (&u)[9]) {
+    // row2 = conj(row0 x row1), exact for SU(3)
+    Cx<R> a = cmul(u[1], u[5]), b = cmul(u[2], u[4]);
+    u[6] = {a.re - b.re, -(a.im - b.im)};
+    a = cmul(u[2], u[3]);
+    b = cmul(u[0], u[5]);
+    u[7] = {a.re - b.re, -(a.im - b.im)};
+    a = cmul(u[0], u[4]);
+    b = cmul(u[1], u[3]);
+    u[8] = {a.re - b.re, -(a.im - b.im)};
+}
+
+template <int RECON>
+struct LinkIO<COLA_F64, RECON> {
+    __device__ static __forceinline__ void load(const void *dir_base, int vh, int cb, Cx<double> (&u)[9]) {
+        const double2 *p = reinterpret_cast<const double2 *>(dir_base);
+        constexpr int n = RECON == 12 ? 6 : 9;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            double2 v = __ldg(p + (size_t)k * vh + cb);
+            u[k] = {v.x, v.y};
+        }
+        if constexpr (RECON == 12) reconstruct_row2(u);
+    }
+};
+
+template <int RECON>
+struct LinkIO<COLA_F32, RECON> {
+    __device__ static __forceinline__ void load(const void *dir_base, int vh, int cb, Cx<float> (&u)[9]) {
+        const float4 *p = reinterpret_cast<const float4 *>(dir_base);
+        if constexpr (RECON == 12) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float4 v = __ldg(p + (size_t)k * vh + cb);
+                u[2 * k] = {v.x, v.y};
+                u[2 * k + 1] = {v.z, v.w};
+            }
+            reconstruct_row2(u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 v = __ldg(p + (size_t)k * vh + cb);
+                u[2 * k] = {v.x, v.y};
+                u[2 * k + 1] = {v.z, v.w};
+            }
+            float4 v = __ldg(p + (size_t)4 * vh + cb);
+            u[8] = {v.x, v.y};
+        }
+    }
+};
+
+template <int RECON>
+struct LinkIO<COLA_F16, RECON> {
+    __device__ static __forceinline__ void load(const void *dir_base, int vh, int cb, Cx<float> (&u)[9]) {
+        const uint2 *p = reinterpret_cast<const uint2 *>(dir_base);
+        constexpr int n = RECON == 12 ? 3 : 5;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            uint2 v = __ldg(p + (size_t)k * vh + cb);
+            float2 a = h2f(v.x), b = h2f(v.y);
+            if (2 * k < 9) u[2 * k] = {a.x, a.y};
+            if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
+        }
+        if constexpr (RECON == 12) reconstruct_row2(u);
+    }
+};
+
+// ------------------------------------------------------------- reductions --
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block in a fixed order; the result is valid in thread 0.
+// `sh` must hold at least 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        const int nw = (nthreads + 31) >> 5;
+        r = lane < nw ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+}  // namespace cola
+
+namespace cola {
+
+// ------------------------------------------------------ solver state (device) --
+// One per right-hand side; all CG scalars live on the device so that the
+// iteration needs no host round trip.
+struct CgState {
+    double rho;      // <r, r> of the residual the current alpha uses
+    double rho_new;  // <r, r> after the latest update
+    double pq;       // <p, A p> = |M p|^2
+    double alpha;
+    double r2_last;  // |r_hi|^2 at the last reliable update (FP64 true residual)
+    double b2;       // |b|^2
+    double tol2;     // tol^2 |b|^2
+    double delta2;   // delta^2
+    int iter;
+    int max_iter;
+    int ru;          // a reliable update is due
+    int ru_count;
+    int done;
+    int status;
+};
+
+// Sum over the threads of each row threadIdx.y of the block, fixed order.
+// blockDim.x must be a multiple of 32.  The sum is valid in threadIdx.x == 0.
+__device__ __forceinline__ double row_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31;
+    const int wrow = threadIdx.x >> 5;
+    const int wpr = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[threadIdx.y * wpr + wrow] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < wpr; ++w) r += sh[threadIdx.y * wpr + w];
+    }
+    return r;
+}
+
+// Two-stage deterministic reduction: every block writes its row sums to
+// partials[row][block]; the last block to arrive (atomic ticket) sums each
+// row's partials in block order.  Returns true in the threads of the last
+// block; `out[row]` then holds the sum of that row (valid in threadIdx.x == 0).
+// `counter` is reset by the last block so the next launch starts from zero.
+__device__ __forceinline__ bool reduce_rows_last_block(double v, double *partials, unsigned *counter,
+                                                       int nblocks, int block_id, int row_global,
+                                                       bool row_valid, double *sh, double *out_row_sum) {
+    __shared__ bool am_last;
+    double s = row_sum(v, sh);
+    if (threadIdx.x == 0 && row_valid) partials[(size_t)row_global * nblocks + block_id] = s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        unsigned ticket = atomicAdd(counter, 1u);
+        am_last = (ticket == (unsigned)nblocks - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    // each row's 32 lanes of warp 0 of that row sum the partials in a fixed pattern
+    double acc = 0.0;
+    if (row_valid) {
+        const volatile double *pr = partials + (size_t)row_global * nblocks;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += pr[b];
+    }
+    double tot = row_sum(acc, sh);
+    if (threadIdx.x == 0) *out_row_sum = tot;
+    if (threadIdx.x == 0 && threadIdx.y == 0) *counter = 0u;
+    return true;
+}
+
+}  // namespace cola

@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads and exports what include/cola.h declares (CPU only).
+
+Also checks host-side argument validation, which runs before any CUDA call,
+and that the ctypes structures match the C layout (compiled with gcc).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cola.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cola_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_00850_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ["cola_dslash_apply", "cola_mdagm_apply", "cola_cg_solve", "cola_fermion_force"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2302_00850_gb300 import _lib
+
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature"
+
+
+def test_struct_layout_matches_c(tmp_path):
+    from paper_2302_00850_gb300 import _lib
+
+    prog = tmp_path / "sz.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "cola.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(cola_lattice), sizeof(cola_gauge_opts),"
+        " sizeof(cola_solver_params), sizeof(cola_solve_info), offsetof(cola_solver_params, delta),"
+        " offsetof(cola_solve_info, true_rel_resid), offsetof(cola_lattice, bc));return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(_lib.Lattice), ctypes.sizeof(_lib.GaugeOpts), ctypes.sizeof(_lib.SolverParams),
+            ctypes.sizeof(_lib.SolveInfo), _lib.SolverParams.delta.offset, _lib.SolveInfo.true_rel_resid.offset,
+            _lib.Lattice.bc.offset]
+    assert got == want
+
+
+def _lattice(dims, kappa=0.12):
+    from paper_2302_00850_gb300 import _lib
+
+    lat = _lib.Lattice()
+    for m in range(4):
+        lat.dims[m] = dims[m]
+        lat.bc[m][0] = 1.0
+    lat.bc[3][0] = -1.0
+    lat.kappa = kappa
+    return lat
+
+
+def test_spinor_bytes(lib):
+    lat = _lattice((4, 4, 4, 8))
+    v = 4 * 4 * 4 * 8
+    assert lib.cola_spinor_bytes(ctypes.byref(lat), 0, 1) == v * 192
+    assert lib.cola_spinor_bytes(ctypes.byref(lat), 1, 3) == 3 * v * 96
+    assert lib.cola_spinor_bytes(ctypes.byref(lat), 2, 2) == 2 * v * 52
+    assert lib.cola_spinor_bytes(ctypes.byref(_lattice((4, 5, 4, 8))), 0, 1) == 0
+
+
+def test_argument_errors_before_any_cuda_call(lib):
+    from paper_2302_00850_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    opts = _lib.GaugeOpts()
+    opts.prec_mask = 1
+    opts.recon[0] = 18
+    dummy = ctypes.c_void_p(1)
+    assert lib.cola_gauge_create(ctypes.byref(_lattice((4, 3, 4, 4))), dummy, ctypes.byref(opts), None,
+                                 ctypes.byref(h)) == -1
+    assert b"even" in lib.cola_last_error()
+    opts.recon[0] = 14
+    assert lib.cola_gauge_create(ctypes.byref(_lattice((4, 4, 4, 4))), dummy, ctypes.byref(opts), None,
+                                 ctypes.byref(h)) == -1
+    assert b"recon" in lib.cola_last_error()
+    opts.prec_mask = 0
+    assert lib.cola_gauge_create(ctypes.byref(_lattice((4, 4, 4, 4))), dummy, ctypes.byref(opts), None,
+                                 ctypes.byref(h)) == -1
+    assert lib.cola_cg_solve(None, None, None, None, None, None) == -1
+    assert lib.cola_dslash_apply(None, None, None, None, 0.0, 1.0, 0, 0, 0, 1, None) == -1
+    assert lib.cola_gauge_destroy(None) == 0
