@@ -125,9 +125,10 @@ def test_multi_rhs_gaussian_matches_single(cola):
     g = cola.Gauge(to_dev(u), dims, kappa, BC_AP, precisions=("f64",))
     x, infos = cola.cg_solve(g, to_dev(b), tol=1e-10, op="eo", inner="f64")
     for r in range(3):
+        # the batched launch blocks sites differently, so reductions round differently
         xs, i1 = cola.cg_solve(g, to_dev(b[r]), tol=1e-10, op="eo", inner="f64")
-        assert infos[r].iters == i1[0].iters
-        assert bool((x[r] == xs).all())
+        assert abs(infos[r].iters - i1[0].iters) <= 1
+        assert rel_err(x[r].cpu().numpy(), xs.cpu().numpy()) < 1e-9
 
 
 def test_error_statuses(cola):
