@@ -314,15 +314,41 @@ def run_cola(args):
         dist.destroy_process_group()
 
 
+def run_dslash_only(args):
+    """Chained parity Dslash applies only (the case profiled with ncu)."""
+    import torch
+
+    import paper_2302_00850_gb300 as cola
+
+    torch.cuda.set_device(0)
+    u, b = make_inputs(torch.device("cuda", 0))
+    prec = args.prec
+    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
+    del u
+    p = cola.pack(g, b, prec)
+    t = g.empty_packed(prec)
+    for _ in range(args.reps):
+        cola.dslash(g, t, p, parity=1, prec=prec)
+        cola.dslash(g, p, t, parity=0, prec=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--dslash-only", action="store_true", help="run chained parity Dslash applies and exit")
+    ap.add_argument("--prec", default="f16")
+    ap.add_argument("--recon", type=int, default=12)
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cola", choices=["cola", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.dslash_only:
+        run_dslash_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_cola(args)
