@@ -113,6 +113,21 @@ cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const voi
 cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
                              int nrhs, cudaStream_t stream);
 
+/* The same operator as cola_mdagm_apply, for callers that cannot allocate
+ * device memory when they call it (for example code being captured into a
+ * CUDA graph, where cudaMalloc is not allowed, or a service that reserves all
+ * device memory up front).  The paper has no counterpart: it is an addition
+ * of this library.  It calls no allocator; its temporaries live in one
+ * static device array of 64 MiB that the library holds on each device until
+ * the process exits.  A call needs cola_spinor_bytes(lat, prec, nrhs) bytes
+ * of that array and returns COLA_ERR_ARG above 64 MiB.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, unordered threads) race, so order them. */
+cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
+                                     int nrhs, cudaStream_t stream);
+
 typedef struct {
     double tol;      /* target true relative residual (e.g. 1e-10) */
     int max_iter;    /* iteration cap (CG steps) */

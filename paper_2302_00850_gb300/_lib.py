@@ -63,6 +63,7 @@ SIGNATURES = {
     "cola_spinor_unpack": (_st, [_vp, _vp, _vp, _i, _i, _vp]),
     "cola_dslash_apply": (_st, [_vp, _vp, _vp, _vp, _d, _d, _i, _i, _i, _i, _vp]),
     "cola_mdagm_apply": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "cola_mdagm_apply_noalloc": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "cola_cg_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_fermion_force": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_dirac_link_grad": (_st, [_vp, _vp, _vp, _vp, _vp]),
