@@ -157,6 +157,16 @@ cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev,
                           const cola_solver_params *params, cola_solve_info *info,
                           cudaStream_t stream);
 
+/* Several lattices (up to 8, uneven volumes allowed) solved together: every
+ * kernel of an iteration is one launch over all lattices and right-hand sides,
+ * each (lattice, right-hand side) with its own CG scalars and convergence.
+ * gauges[l], x_dev[l], b_dev[l] as in cola_cg_solve (distinct handles, the
+ * same link reconstruction per precision); params (including nrhs) shared;
+ * info has nlat * nrhs entries, lattice-major (host). */
+cola_status cola_cg_solve_batched(int nlat, const cola_gauge *gauges, void *const *x_dev,
+                                  const void *const *b_dev, const cola_solver_params *params,
+                                  cola_solve_info *info, cudaStream_t stream);
+
 /* Fermion force of S = phi^dag (D^dag D)^-1 phi given X = (D^dag D)^-1 phi and
  * Y = D X (canonical FP64, device).  Output force_dev: real FP64 [4][V][8],
  * F^a_mu(x) = dS/d eps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x), T^a = lambda^a/2:

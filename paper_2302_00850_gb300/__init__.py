@@ -10,7 +10,7 @@ hand-written sm_103a kernels (include/cola.h), and this thin torch binding.
     x, info = cola.cg_solve(g, b, op="eo", inner="f16", delta=0.1)
 """
 from .api import (  # noqa: F401
-    ColaError, Gauge, SolveInfo, apply_dirac, cg_solve, dirac_link_grad, dslash, fermion_force, mdagm, pack,
+    ColaError, Gauge, SolveInfo, apply_dirac, cg_solve, cg_solve_batched, dirac_link_grad, dslash, fermion_force, mdagm, pack,
     unpack, F16, F32, F64, OP_EO, OP_FULL, SYS_DIRAC, SYS_NORMAL,
 )
 from .autograd import DiracOp, PseudofermionAction, SolveNormal  # noqa: F401

@@ -65,6 +65,8 @@ SIGNATURES = {
     "cola_mdagm_apply": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "cola_mdagm_apply_noalloc": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "cola_cg_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
+    "cola_cg_solve_batched": (_st, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                     ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_fermion_force": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_dirac_link_grad": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_last_error": (ctypes.c_char_p, []),

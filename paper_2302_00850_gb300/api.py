@@ -174,6 +174,39 @@ def cg_solve(g: Gauge, b: torch.Tensor, x0: torch.Tensor | None = None, tol=1e-1
     return x, res
 
 
+def cg_solve_batched(gauges, bs, x0s=None, tol=1e-10, max_iter=100000, op="eo", system="normal", inner="f64",
+                     delta=0.1, use_graph=False, raise_on_error=True):
+    """Solve several lattices together (cola_cg_solve_batched).
+
+    gauges: list of Gauge (distinct, same device); bs: matching list of sources,
+    each with the same number of right-hand sides.  Returns (xs, infos) with
+    infos[l][r] the SolveInfo of lattice l, right-hand side r.
+    """
+    nlat = len(gauges)
+    if nlat != len(bs) or nlat < 1:
+        raise ValueError("gauges and bs must be non-empty lists of the same length")
+    nrhs = _nrhs_of(gauges[0], bs[0])
+    xs = []
+    for l, (g, b) in enumerate(zip(gauges, bs)):
+        if _nrhs_of(g, b) != nrhs:
+            raise ValueError("every lattice of a batch must have the same number of right-hand sides")
+        _complex_field(b, nrhs * g.volume * 12, "b")
+        xs.append(torch.zeros_like(b) if x0s is None else x0s[l].clone())
+    lib = gauges[0].lib
+    hs = (ctypes.c_void_p * nlat)(*[g.handle.value for g in gauges])
+    xp = (ctypes.c_void_p * nlat)(*[_ptr(x) for x in xs])
+    bp = (ctypes.c_void_p * nlat)(*[_ptr(b) for b in bs])
+    prm = _lib.SolverParams(float(tol), int(max_iter), OPS[op], SYSTEMS[system], PREC[inner], float(delta), nrhs,
+                            int(bool(use_graph)))
+    infos = (_lib.SolveInfo * (nlat * nrhs))()
+    st = lib.cola_cg_solve_batched(nlat, hs, xp, bp, ctypes.byref(prm), infos, _stream(gauges[0].device))
+    res = [[SolveInfo(i.iters, i.reliable_updates, i.true_rel_resid, i.seconds, i.status)
+            for i in infos[l * nrhs:(l + 1) * nrhs]] for l in range(nlat)]
+    if st != 0 and (raise_on_error or st not in (-4, -5)):
+        check(st)
+    return xs, res
+
+
 def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
     """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X."""
     lx, ly, lz, lt = g.dims

@@ -88,8 +88,8 @@ cola_status ws_slot(cola_gauge g, int k, size_t bytes, void **out) {
     return COLA_OK;
 }
 
-cola_status ws_reduce(cola_gauge g, size_t nrows, size_t nblocks) {
-    const size_t need = nrows * nblocks;
+cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride, size_t ncounters) {
+    const size_t need = nrows * pstride;
     if (g->partials_count < need) {
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
@@ -97,13 +97,14 @@ cola_status ws_reduce(cola_gauge g, size_t nrows, size_t nblocks) {
         COLA_CUDA(cudaMalloc(&g->partials, need * sizeof(double)), "reduction scratch");
         g->partials_count = need;
     }
-    if (g->counters_count < nrows) {
+    const size_t nc = ncounters > nrows ? ncounters : nrows;
+    if (g->counters_count < nc) {
         if (g->counters) cudaFree(g->counters);
         g->counters = nullptr;
         g->counters_count = 0;
-        COLA_CUDA(cudaMalloc(&g->counters, nrows * sizeof(unsigned)), "reduction counters");
-        COLA_CUDA(cudaMemset(g->counters, 0, nrows * sizeof(unsigned)), "reduction counters");
-        g->counters_count = nrows;
+        COLA_CUDA(cudaMalloc(&g->counters, nc * sizeof(unsigned)), "reduction counters");
+        COLA_CUDA(cudaMemset(g->counters, 0, nc * sizeof(unsigned)), "reduction counters");
+        g->counters_count = nc;
     }
     return COLA_OK;
 }
@@ -128,69 +129,97 @@ static int rhs_per_block_for(int nrhs) {
     return 4;
 }
 
-DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
-                            int parity0, double a, double b) {
+DslashLat make_dslash_lat(cola_gauge g, int prec, void *out, const void *in, const void *xin, double a, double b,
+                          int row0) {
+    DslashLat L;
+    std::memset(&L, 0, sizeof(L));
+    L.g = g->geom;
+    L.links = g->links[prec];
+    L.link_parity_stride = g->link_parity_bytes[prec];
+    L.link_dir_stride = link_dir_bytes(prec, g->recon[prec], g->geom.Vh);
+    L.out = out;
+    L.in = in;
+    L.xin = xin;
+    L.parity_stride = spinor_parity_bytes(prec, g->geom.Vh);
+    L.rhs_stride = 2 * L.parity_stride;
+    L.a = a;
+    L.b = b;
+    L.row0 = row0;
+    return L;
+}
+
+static DslashArgs empty_args(int nrhs, int parity0) {
     DslashArgs A;
     std::memset(&A, 0, sizeof(A));
-    A.g = g->geom;
-    A.out = out;
-    A.in = in;
-    A.xin = xin;
-    A.links = g->links[prec];
-    A.link_parity_stride = g->link_parity_bytes[prec];
-    A.link_dir_stride = link_dir_bytes(prec, g->recon[prec], g->geom.Vh);
-    A.parity_stride = spinor_parity_bytes(prec, g->geom.Vh);
-    A.rhs_stride = 2 * A.parity_stride;
-    A.parity0 = parity0;
     A.nrhs = nrhs;
     A.rhs_per_block = rhs_per_block_for(nrhs);
-    A.a = a;
-    A.b = b;
+    A.parity0 = parity0;
     return A;
 }
 
-static cola_status dslash_launch(cola_gauge g, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
-                                 bool red, cudaStream_t s) {
+DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
+                            int parity0, double a, double b) {
+    DslashArgs A = empty_args(nrhs, parity0);
+    A.nlat = 1;
+    A.lat[0] = make_dslash_lat(g, prec, out, in, xin, a, b, 0);
+    return A;
+}
+
+cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+                          cudaStream_t s) {
     if (red) {
-        const int bx = default_dslash_block(prec, A.rhs_per_block);
-        const size_t nblocks = (size_t)((g->geom.Vh + bx - 1) / bx) * nparity;
-        const size_t ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
-        COLA_TRY(ws_reduce(g, A.nrhs > (int)ngroups ? A.nrhs : ngroups, nblocks));
-        A.partials = g->partials;
-        A.counters = g->counters;
+        int pstride, ncounters, nrows = 0;
+        dslash_reduce_shape(A, nparity, default_dslash_block(prec, A.rhs_per_block), &pstride, &ncounters);
+        for (int l = 0; l < A.nlat; ++l)
+            if (A.lat[l].row0 + A.nrhs > nrows) nrows = A.lat[l].row0 + A.nrhs;
+        COLA_TRY(ws_reduce(owner, nrows, pstride, ncounters));
+        A.partials = owner->partials;
+        A.pstride = pstride;
+        A.counters = owner->counters;
     }
-    return cuda_check(launch_dslash(prec, g->recon[prec], A, nparity, dagger, xpay, red, 0, s), "dslash launch");
+    return cuda_check(launch_dslash(prec, owner->recon[prec], A, nparity, dagger, xpay, red, 0, s), "dslash launch");
+}
+
+cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
+                              bool reduce, cudaStream_t s) {
+    cola_gauge owner = L[0].g;
+    auto batch = [&](int parity0, double a_coef, bool use_xin, int which) {
+        // which: 0 in->t, 1 t->mp (xin = in), 2 mp->t, 3 t->out (xin = mp); full: 4 in->mp, 5 mp->out
+        DslashArgs A = empty_args(nrhs, parity0);
+        A.nlat = nlat;
+        A.state = st;
+        A.filter_ru = filter_ru;
+        for (int l = 0; l < nlat; ++l) {
+            const OpLat &o = L[l];
+            const double k = o.g->lat.kappa;
+            const double b = which >= 4 ? -k : (which == 1 || which == 3) ? -k * k : 1.0;
+            void *out = which == 0 || which == 2 ? o.t : which == 1 || which == 4 ? o.mp : o.out;
+            const void *in = which == 0 || which == 4 ? o.in : which == 1 || which == 3 ? o.t : o.mp;
+            const void *xin = !use_xin ? nullptr : (which == 1 || which == 4) ? o.in : o.mp;
+            A.lat[l] = make_dslash_lat(o.g, prec, out, in, xin, a_coef, b, o.row0);
+        }
+        return A;
+    };
+    if (op == COLA_OP_EO) {
+        DslashArgs A = batch(1, 0.0, false, 0);
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, false, false, s));
+        A = batch(0, 1.0, true, 1);
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, true, reduce, s));
+        A = batch(1, 0.0, false, 2);
+        COLA_TRY(dslash_launch(owner, prec, A, 1, true, false, false, s));
+        A = batch(0, 1.0, true, 3);
+        return dslash_launch(owner, prec, A, 1, true, true, false, s);
+    }
+    DslashArgs A = batch(0, 1.0, true, 4);
+    COLA_TRY(dslash_launch(owner, prec, A, 2, false, true, reduce, s));
+    A = batch(0, 1.0, true, 5);
+    return dslash_launch(owner, prec, A, 2, true, true, false, s);
 }
 
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
                         CgState *st, bool filter_ru, bool reduce, cudaStream_t s) {
-    const double k = g->lat.kappa;
-    if (op == COLA_OP_EO) {
-        DslashArgs A = make_dslash_args(g, prec, t, in, nullptr, nrhs, 1, 0.0, 1.0);
-        A.state = st;
-        A.filter_ru = filter_ru;
-        COLA_TRY(dslash_launch(g, prec, A, 1, false, false, false, s));
-        A = make_dslash_args(g, prec, mp, t, in, nrhs, 0, 1.0, -k * k);
-        A.state = st;
-        A.filter_ru = filter_ru;
-        COLA_TRY(dslash_launch(g, prec, A, 1, false, true, reduce, s));
-        A = make_dslash_args(g, prec, t, mp, nullptr, nrhs, 1, 0.0, 1.0);
-        A.state = st;
-        A.filter_ru = filter_ru;
-        COLA_TRY(dslash_launch(g, prec, A, 1, true, false, false, s));
-        A = make_dslash_args(g, prec, out, t, mp, nrhs, 0, 1.0, -k * k);
-        A.state = st;
-        A.filter_ru = filter_ru;
-        return dslash_launch(g, prec, A, 1, true, true, false, s);
-    }
-    DslashArgs A = make_dslash_args(g, prec, mp, in, in, nrhs, 0, 1.0, -k);
-    A.state = st;
-    A.filter_ru = filter_ru;
-    COLA_TRY(dslash_launch(g, prec, A, 2, false, true, reduce, s));
-    A = make_dslash_args(g, prec, out, mp, mp, nrhs, 0, 1.0, -k);
-    A.state = st;
-    A.filter_ru = filter_ru;
-    return dslash_launch(g, prec, A, 2, true, true, false, s);
+    OpLat L = {g, out, in, t, mp, 0};
+    return apply_mdagm_batch(1, &L, prec, op, nrhs, st, filter_ru, reduce, s);
 }
 
 }  // namespace cola

@@ -7,34 +7,50 @@
 
 namespace cola {
 
-// Arguments of one hopping-term launch.  Pointers address whole packed
+// Lattices of one batched launch (a single lattice is a batch of one).
+constexpr int kMaxBatch = 8;
+
+// One lattice of a hopping-term launch.  Spinor pointers address whole packed
 // fields (both parities, right-hand side 0); the kernel offsets them by
 // parity and right-hand side.
-struct DslashArgs {
+struct DslashLat {
     Geom g;
-    void *out;
-    const void *in;
-    const void *xin;              // xpay input, same layout as out (may be null if !xpay)
     const void *links;            // packed links of this precision: [parity][mu][group][Vh]
     size_t link_parity_stride;    // bytes of one parity of links
     size_t link_dir_stride;       // bytes of one direction of one parity
+    void *out;
+    const void *in;
+    const void *xin;              // xpay input, same layout as out (null if !xpay)
     size_t parity_stride;         // bytes of one parity of one spinor field
     size_t rhs_stride;            // bytes of one right-hand side of a spinor field
-    int parity0;                  // first output parity (blockIdx.z adds 0 or 1)
+    double a, b;                  // out = a xin + b H in
+    int row0;                     // solver row (state, partials) of this lattice's rhs 0
+    int block0;                   // first blockIdx.x of this lattice (set by launch_dslash)
+    int nblocks;                  // site blocks of this lattice per parity (set by launch_dslash)
+};
+
+struct DslashArgs {
+    int nlat;
     int nrhs;
     int rhs_per_block;
-    double a, b;
+    int parity0;                  // first output parity (blockIdx.z adds 0 or 1)
+    DslashLat lat[kMaxBatch];
     // fused |out|^2 reduction (when launched with red = true)
-    double *partials;             // [nrhs][nblocks]
-    unsigned *counters;           // one per right-hand-side group, zero between launches
-    double *result;               // [nrhs] sums (when state == nullptr)
+    double *partials;             // [row][pstride]
+    int pstride;
+    unsigned *counters;           // [lattice][rhs group], zero between launches
+    int ngroups;
+    double *result;               // [row] sums (when state == nullptr)
     CgState *state;               // solver mode: skips finished rows; with red, sets pq and alpha
     int filter_ru;                // with state: compute only rows with a pending reliable update
 };
 
 int default_dslash_block(int prec, int rhs_per_block);
-cudaError_t launch_dslash(int prec, int recon, const DslashArgs &A, int nparity, bool dagger, bool xpay,
-                          bool red, int block_x, cudaStream_t s);
+// Fills block0/nblocks of every lattice for block_x and launches.
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+                          int block_x, cudaStream_t s);
+// Largest per-row partials count and counters a launch of A needs.
+void dslash_reduce_shape(const DslashArgs &A, int nparity, int block_x, int *pstride, int *ncounters);
 
 // ---------------------------------------------------------------- packing --
 cudaError_t launch_pack_gauge(int prec, int recon, const Geom &g, void *packed, const void *canon,
@@ -45,45 +61,47 @@ cudaError_t launch_unpack_spinor(int prec, const Geom &g, void *canon, const voi
                                  int parity_mask, cudaStream_t s);
 
 // ------------------------------------------------------------ CG kernels --
-// Vector arguments address a field of `nparity` parity blocks starting at the
-// given pointer (right-hand side 0); rhs_stride/parity_stride in bytes per
-// precision of that vector.
-struct VecRef {
-    void *ptr;
-    int prec;
-    size_t parity_stride;
-    size_t rhs_stride;
-};
+// Batched vector kernels: per lattice up to kMaxVecs packed fields (slot
+// meaning depends on the kernel), all of the precision prec[slot].  Each
+// lattice covers nparity parity blocks (1: even half only; 2: whole lattice)
+// of nrhs right-hand sides; rows are row0 + rhs.
+constexpr int kMaxVecs = 5;
 
-struct BlasDims {
+struct BlasLat {
     int vh;
-    int nparity;   // 1 (even-odd) or 2 (whole lattice)
-    int nrhs;
+    int row0;
+    int block0;    // set by the launcher
+    int nblocks;   // set by the launcher
+    void *v[kMaxVecs];
 };
 
-// x += alpha p; r -= alpha q; rho_new = |r|^2; decides reliable update / stop.
-cudaError_t launch_cg_update_xr(const BlasDims &d, VecRef x, VecRef r, VecRef p, VecRef q, CgState *st,
-                                double *partials, unsigned *counters, cudaStream_t s);
-// p = r + (rho_new / rho) p for rows not done.
-cudaError_t launch_cg_update_p(const BlasDims &d, VecRef p, VecRef r, CgState *st, bool only_ru_rows,
-                               cudaStream_t s);
-// x_hi += x_lo; x_lo = 0 (rows with a pending reliable update, or all rows if force).
-cudaError_t launch_ru_accumulate(const BlasDims &d, VecRef xhi, VecRef xlo, CgState *st, bool force,
-                                 cudaStream_t s);
-// r_hi = b - Ax; r_lo = r_hi; (init: p = r_lo); rho_new = r2_last = |r_hi|^2; convergence.
-cudaError_t launch_ru_residual(const BlasDims &d, VecRef rhi, VecRef b, VecRef ax, VecRef rlo, VecRef p,
-                               CgState *st, bool force, bool init, double *partials, unsigned *counters,
-                               cudaStream_t s);
-// st.b2 = |b|^2 and st.tol2 = tol^2 |b|^2.
-cudaError_t launch_init_norms(const BlasDims &d, VecRef b, CgState *st, double *partials, unsigned *counters,
-                              cudaStream_t s);
-// dst = src with precision conversion (both VecRefs of the same shape).
-cudaError_t launch_convert(const BlasDims &d, VecRef dst, VecRef src, cudaStream_t s);
-// ||v||^2 per right-hand side into out[rhs] (FP64 accumulation).
-cudaError_t launch_norm2(const BlasDims &d, VecRef v, double *out, double *partials, unsigned *counters,
-                         cudaStream_t s);
-// dst = a*x + b*y per right-hand side, any precisions.
-cudaError_t launch_axpby(const BlasDims &d, VecRef dst, double a, VecRef x, double b, VecRef y, cudaStream_t s);
+struct BlasArgs {
+    int nlat;
+    int nparity;
+    int nrhs;
+    int prec[kMaxVecs];
+    BlasLat lat[kMaxBatch];
+    CgState *state;
+    double *partials;
+    int pstride;
+    unsigned *counters;   // one per row
+    double *out;          // norm2 results per row
+    double a, b;          // axpby coefficients
+    int init;             // ru_residual: initial residual (every row, also writes p)
+};
+
+// Slots: update_xr (x, r, p, q); update_p (p, r); ru_accumulate (x_hi, x_lo);
+// ru_residual (r_hi, b, ax, r_lo, p); norm2 (v); convert (dst, src); axpby (dst, x, y).
+cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_ru_accumulate(BlasArgs &B, bool force, cudaStream_t s);
+cudaError_t launch_ru_residual(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_init_norms(BlasArgs &B, cudaStream_t s);   // st.b2 = |b|^2, st.tol2 *= |b|^2
+cudaError_t launch_norm2(BlasArgs &B, cudaStream_t s);        // out[row] = |v|^2
+cudaError_t launch_convert(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_axpby(BlasArgs &B, cudaStream_t s);
+// Per-row partials count the batched vector kernels need.
+int blas_pstride(const BlasArgs &B);
 
 // ----------------------------------------------------------------- force --
 cudaError_t launch_force(const Geom &g, double kappa, const void *links_f64, int recon, double *force,
@@ -122,16 +140,34 @@ struct cola_gauge_s {
 namespace cola {
 // Device buffer of at least `bytes` in workspace slot `k` (grown if needed).
 cola_status ws_slot(cola_gauge g, int k, size_t bytes, void **out);
-// Reduction scratch for up to `nrows` rows of `nblocks` partials.
-cola_status ws_reduce(cola_gauge g, size_t nrows, size_t nblocks);
+// Reduction scratch: nrows rows of pstride partials and ncounters counters.
+cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride, size_t ncounters);
 cola_status ws_states(cola_gauge g, int n);
 
+// One lattice of an operator application: out = M^dag M in with temporaries
+// t and mp (full packed fields of the same precision), solver rows from row0.
+struct OpLat {
+    cola_gauge g;
+    void *out;
+    const void *in;
+    void *t;
+    void *mp;
+    int row0;
+};
+
+DslashLat make_dslash_lat(cola_gauge g, int prec, void *out, const void *in, const void *xin, double a, double b,
+                          int row0);
 DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
                             int parity0, double a, double b);
-// out = Mdag M in (op EO: Mhat on even halves; op FULL: D).  t and mp are
-// full-field temporaries of the same precision.  With st != nullptr the
-// first xpay apply reduces |M in|^2 into st (pq, alpha), and rows are
-// filtered by st (filter_ru: only rows with a pending reliable update).
+// Launch a (batched) hopping term; reduction scratch comes from `owner`.
+cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
+                          bool red, cudaStream_t s);
+// out = Mdag M in for every lattice of L (op EO: Mhat on even halves; op
+// FULL: D).  With st != nullptr rows are filtered by st (filter_ru: only rows
+// with a pending reliable update) and, with reduce, the first xpay apply
+// reduces |M in|^2 into st (pq, alpha).  Scratch comes from L[0].g.
+cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
+                              bool reduce, cudaStream_t s);
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
                         CgState *st, bool filter_ru, bool reduce, cudaStream_t s);
 cola_status cuda_check(cudaError_t e, const char *what);

@@ -145,6 +145,11 @@ struct SpinorIO;
 
 template <>
 struct SpinorIO<COLA_F64> {
+    // values without any site scale, and the scale (1 unless FP16)
+    __device__ static __forceinline__ double load_raw(const void *base, int vh, int cb, Cx<double> (&s)[12]) {
+        load(base, vh, cb, s);
+        return 1.0;
+    }
     __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<double> (&s)[12]) {
         const double2 *p = reinterpret_cast<const double2 *>(base);
 #pragma unroll
@@ -162,6 +167,10 @@ struct SpinorIO<COLA_F64> {
 
 template <>
 struct SpinorIO<COLA_F32> {
+    __device__ static __forceinline__ float load_raw(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
+        load(base, vh, cb, s);
+        return 1.0f;
+    }
     __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
         const float4 *p = reinterpret_cast<const float4 *>(base);
 #pragma unroll
@@ -190,6 +199,20 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
 
 template <>
 struct SpinorIO<COLA_F16> {
+    __device__ static __forceinline__ float load_raw(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(base);
+        const float sc = __ldg(reinterpret_cast<const float *>(p + (size_t)3 * vh) + cb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = __ldg(p + (size_t)k * vh + cb);
+            float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+            s[4 * k + 0] = {a.x, a.y};
+            s[4 * k + 1] = {b.x, b.y};
+            s[4 * k + 2] = {c.x, c.y};
+            s[4 * k + 3] = {d.x, d.y};
+        }
+        return sc;
+    }
     __device__ static __forceinline__ void load(const void *base, int vh, int cb, Cx<float> (&s)[12]) {
         const uint4 *p = reinterpret_cast<const uint4 *>(base);
         const float sc = __ldg(reinterpret_cast<const float *>(p + (size_t)3 * vh) + cb);
@@ -367,16 +390,17 @@ __device__ __forceinline__ double row_sum(double v, double *sh) {
 }
 
 // Two-stage deterministic reduction: every block writes its row sums to
-// partials[row][block]; the last block to arrive (atomic ticket) sums each
-// row's partials in block order.  Returns true in the threads of the last
-// block; `out[row]` then holds the sum of that row (valid in threadIdx.x == 0).
-// `counter` is reset by the last block so the next launch starts from zero.
-__device__ __forceinline__ bool reduce_rows_last_block(double v, double *partials, unsigned *counter,
-                                                       int nblocks, int block_id, int row_global,
+// partials[row * pstride + block_id]; the last block of the row group to
+// arrive (atomic ticket) sums each row's partials in block order.  Returns
+// true in the threads of the last block; `*out_row_sum` then holds the sum of
+// the calling thread's row (valid in threadIdx.x == 0).  `counter` is reset by
+// the last block, so the next launch starts from zero.
+__device__ __forceinline__ bool reduce_rows_last_block(double v, double *partials, int pstride, int row_global,
+                                                       unsigned *counter, int nblocks, int block_id,
                                                        bool row_valid, double *sh, double *out_row_sum) {
     __shared__ bool am_last;
     double s = row_sum(v, sh);
-    if (threadIdx.x == 0 && row_valid) partials[(size_t)row_global * nblocks + block_id] = s;
+    if (threadIdx.x == 0 && row_valid) partials[(size_t)row_global * pstride + block_id] = s;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -386,10 +410,9 @@ __device__ __forceinline__ bool reduce_rows_last_block(double v, double *partial
     __syncthreads();
     if (!am_last) return false;
     __threadfence();
-    // each row's 32 lanes of warp 0 of that row sum the partials in a fixed pattern
     double acc = 0.0;
     if (row_valid) {
-        const volatile double *pr = partials + (size_t)row_global * nblocks;
+        const volatile double *pr = partials + (size_t)row_global * pstride;
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += pr[b];
     }
     double tot = row_sum(acc, sh);

@@ -15,7 +15,13 @@
 // projector has rank two, so the SU(3) multiply acts on a two-spinor and
 // the other two spin rows are rebuilt from it (spin projection and
 // reconstruction, gamma matrices in the DeGrand-Rossi basis).
+#include <cstdlib>
+
 #include "cola_impl.h"
+
+#ifndef COLA_DSLASH_MINB
+#define COLA_DSLASH_MINB 2
+#endif
 
 namespace cola {
 
@@ -58,33 +64,38 @@ __device__ __forceinline__ Cx<R> times_i(Cx<R> a, int s) {  // s*i*a
     return s > 0 ? Cx<R>{-a.im, a.re} : Cx<R>{a.im, -a.re};
 }
 
-// acc += full spinor rebuilt from w = U h (rows 2, 3 follow from rows 0, 1).
+// acc += sc * (full spinor rebuilt from w = U h); rows 2, 3 follow from rows 0, 1.
+// sc carries the neighbour's FP16 site scale and a real boundary phase, so
+// both cost nothing beyond the fused multiply-adds of the accumulation.
 template <int MU, int S, typename R>
-__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3]) {
+__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3], R sc) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        acc[a].re += w[0][a].re;
-        acc[a].im += w[0][a].im;
-        acc[3 + a].re += w[1][a].re;
-        acc[3 + a].im += w[1][a].im;
-        Cx<R> r2, r3;
-        if constexpr (MU == 0) {         // r2 = -S i w1, r3 = -S i w0
-            r2 = times_i(w[1][a], -S);
-            r3 = times_i(w[0][a], -S);
+        acc[a].re = fma(sc, w[0][a].re, acc[a].re);
+        acc[a].im = fma(sc, w[0][a].im, acc[a].im);
+        acc[3 + a].re = fma(sc, w[1][a].re, acc[3 + a].re);
+        acc[3 + a].im = fma(sc, w[1][a].im, acc[3 + a].im);
+        if constexpr (MU == 0) {         // r2 = -S i w1, r3 = -S i w0;  i(x + iy) = -y + ix
+            acc[6 + a].re = fma(S * sc, w[1][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, w[1][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, w[0][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, w[0][a].re, acc[9 + a].im);
         } else if constexpr (MU == 1) {  // r2 = S w1, r3 = -S w0
-            r2 = {S * w[1][a].re, S * w[1][a].im};
-            r3 = {-S * w[0][a].re, -S * w[0][a].im};
+            acc[6 + a].re = fma(S * sc, w[1][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, w[1][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, w[0][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, w[0][a].im, acc[9 + a].im);
         } else if constexpr (MU == 2) {  // r2 = -S i w0, r3 = S i w1
-            r2 = times_i(w[0][a], -S);
-            r3 = times_i(w[1][a], S);
+            acc[6 + a].re = fma(S * sc, w[0][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, w[0][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, w[1][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, w[1][a].re, acc[9 + a].im);
         } else {                         // r2 = S w0, r3 = S w1
-            r2 = {S * w[0][a].re, S * w[0][a].im};
-            r3 = {S * w[1][a].re, S * w[1][a].im};
+            acc[6 + a].re = fma(S * sc, w[0][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, w[0][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, w[1][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, w[1][a].im, acc[9 + a].im);
         }
-        acc[6 + a].re += r2.re;
-        acc[6 + a].im += r2.im;
-        acc[9 + a].re += r3.re;
-        acc[9 + a].im += r3.im;
     }
 }
 
@@ -123,8 +134,18 @@ __device__ __forceinline__ void phase_mul(Cx<R> (&w)[2][3], R pr, R pi) {
         for (int a = 0; a < 3; ++a) w[k][a] = cmul(w[k][a], Cx<R>{pr, pi});
 }
 
+// Scale of a hop crossing the boundary: a real phase folds into sc, a
+// complex one multiplies w.
+template <typename R>
+__device__ __forceinline__ void boundary_phase(const Geom &g, int mu, bool conj_phase, Cx<R> (&w)[2][3], R &sc) {
+    const R pr = (R)g.bc[mu][0];
+    const R pi = conj_phase ? -(R)g.bc[mu][1] : (R)g.bc[mu][1];
+    if (pi == R(0)) sc *= pr;
+    else phase_mul(w, pr, pi);
+}
+
 template <int P, int RECON, int MU, bool DAGGER>
-__device__ __forceinline__ void hop_mu(const DslashArgs &A, const Coord &c, int cb, const char *in,
+__device__ __forceinline__ void hop_mu(const DslashLat &A, const Coord &c, int cb, const char *in,
                                        const char *links_out, const char *links_in,
                                        Cx<typename Prec<P>::real> (&acc)[12]) {
     using R = typename Prec<P>::real;
@@ -134,67 +155,251 @@ __device__ __forceinline__ void hop_mu(const DslashArgs &A, const Coord &c, int 
     {
         const int nb = nbr_cb<MU, +1>(g, c, cb);
         Cx<R> psi[12];
-        SpinorIO<P>::load(in, g.Vh, nb, psi);
+        R sc = SpinorIO<P>::load_raw(in, g.Vh, nb, psi);
         Cx<R> h[2][3];
         project<MU, SF>(psi, h);
         Cx<R> u[9];
         LinkIO<P, RECON>::load(links_out + MU * A.link_dir_stride, g.Vh, cb, u);
         Cx<R> w[2][3];
         su3_mul(u, h, w);
-        if (!g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1)
-            phase_mul(w, (R)g.bc[MU][0], (R)g.bc[MU][1]);
-        accumulate<MU, SF>(acc, w);
+        if (!g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1) boundary_phase(g, MU, false, w, sc);
+        accumulate<MU, SF>(acc, w, sc);
     }
     {
         const int nb = nbr_cb<MU, -1>(g, c, cb);
         Cx<R> psi[12];
-        SpinorIO<P>::load(in, g.Vh, nb, psi);
+        R sc = SpinorIO<P>::load_raw(in, g.Vh, nb, psi);
         Cx<R> h[2][3];
         project<MU, SB>(psi, h);
         Cx<R> u[9];
         LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nb, u);
         Cx<R> w[2][3];
         su3_adj_mul(u, h, w);
-        if (!g.bc_trivial[MU] && coord_of<MU>(c) == 0)
-            phase_mul(w, (R)g.bc[MU][0], -(R)g.bc[MU][1]);
-        accumulate<MU, SB>(acc, w);
+        if (!g.bc_trivial[MU] && coord_of<MU>(c) == 0) boundary_phase(g, MU, true, w, sc);
+        accumulate<MU, SB>(acc, w, sc);
     }
 }
 
-// Grid: x over checkerboard sites, y over right-hand-side groups, z over the
-// output parities (1 or 2).  Block: (sites, right-hand sides).
-template <int P, int RECON, bool DAGGER, bool XPAY, bool RED>
-__global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A) {
+// ------------------------------------------------------------------ staged --
+// The FP16/FP32 kernels are limited by how many bytes each SM keeps in
+// flight, not by arithmetic: a thread that loads one hop at a time leaves
+// HBM idle.  The staged variant has each thread copy the raw bytes of its
+// next NSTAGE-1 hops (neighbour spinor, its FP16 scale, the link) into its
+// own shared-memory slots with asynchronous copies (cp.async), then computes
+// hop j from shared memory while hops j+1.. are in flight.  Copies do not
+// occupy registers, so the pipeline depth is not bounded by the register
+// file.  Each thread reads only what it copied itself, so completion needs
+// cp.async.wait_group only, no block barrier.  Shared layout per stage:
+// [chunk][thread] so that a warp's 16-byte reads are conflict-free.
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Raw bytes of one hop: spinor chunks of 16 B (+ one 4-byte FP16 scale) and
+// link chunks of 16 B (FP32) or 8 B (FP16).
+template <int P, int RECON>
+struct HopLayout {
+    static constexpr int spin16 = P == COLA_F32 ? 6 : 3;
+    static constexpr int scale4 = P == COLA_F16 ? 1 : 0;
+    static constexpr int link_chunks = RECON == 12 ? 3 : 5;
+    static constexpr int link_bytes = P == COLA_F32 ? 16 : 8;
+    static constexpr int bytes = spin16 * 16 + scale4 * 4 + link_chunks * link_bytes;
+};
+
+template <int P, int RECON>
+struct Stage {
+    using L = HopLayout<P, RECON>;
+    char *base;  // this stage's area
+    int T;       // threads per block
+    __device__ uint4 *spin(int k, int tid) const { return reinterpret_cast<uint4 *>(base) + k * T + tid; }
+    __device__ float *scale(int tid) const {
+        return reinterpret_cast<float *>(base + L::spin16 * 16 * T) + tid;
+    }
+    __device__ char *link(int k, int tid) const {
+        return base + (L::spin16 * 16 + L::scale4 * 4) * T + (k * T + tid) * L::link_bytes;
+    }
+};
+
+// hop j = 2*mu + (0 forward, 1 backward)
+template <int J>
+struct Hop {
+    static constexpr int MU = J / 2;
+    static constexpr int DIR = (J % 2 == 0) ? +1 : -1;
+};
+
+template <int P, int RECON, int J>
+__device__ __forceinline__ void stage_issue(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *links_out, const char *links_in, const Stage<P, RECON> &st,
+                                            int tid) {
+    using L = HopLayout<P, RECON>;
+    constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
+    const Geom &g = A.g;
+    const int nb = nbr_cb<MU, DIR>(g, c, cb);
+#pragma unroll
+    for (int k = 0; k < L::spin16; ++k) cp_async16(st.spin(k, tid), in + ((size_t)k * g.Vh + nb) * 16);
+    if constexpr (L::scale4) cp_async4(st.scale(tid), in + (size_t)L::spin16 * 16 * g.Vh + (size_t)nb * 4);
+    const char *lb = (DIR > 0 ? links_out : links_in) + MU * A.link_dir_stride;
+    const int lcb = DIR > 0 ? cb : nb;
+#pragma unroll
+    for (int k = 0; k < L::link_chunks; ++k) {
+        const char *src = lb + ((size_t)k * g.Vh + lcb) * L::link_bytes;
+        if constexpr (L::link_bytes == 16) cp_async16(st.link(k, tid), src);
+        else cp_async8(st.link(k, tid), src);
+    }
+}
+
+template <int P, int RECON, int J, bool DAGGER>
+__device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c, const Stage<P, RECON> &st,
+                                              int tid, Cx<float> (&acc)[12]) {
+    using L = HopLayout<P, RECON>;
+    constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
+    constexpr int SF = DAGGER ? +1 : -1;
+    constexpr int S = DIR > 0 ? SF : -SF;
+    const Geom &g = A.g;
+    Cx<float> psi[12];
+    float sc = 1.0f;
+    if constexpr (P == COLA_F16) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 v = *st.spin(k, tid);
+            float2 a = h2f(v.x), b = h2f(v.y), cc = h2f(v.z), d = h2f(v.w);
+            psi[4 * k + 0] = {a.x, a.y};
+            psi[4 * k + 1] = {b.x, b.y};
+            psi[4 * k + 2] = {cc.x, cc.y};
+            psi[4 * k + 3] = {d.x, d.y};
+        }
+        sc = *st.scale(tid);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(st.spin(k, tid));
+            psi[2 * k] = {v.x, v.y};
+            psi[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    Cx<float> h[2][3];
+    project<MU, S>(psi, h);
+    Cx<float> u[9];
+    if constexpr (P == COLA_F16) {
+#pragma unroll
+        for (int k = 0; k < L::link_chunks; ++k) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(st.link(k, tid));
+            float2 a = h2f(v.x), b = h2f(v.y);
+            if (2 * k < 9) u[2 * k] = {a.x, a.y};
+            if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::link_chunks; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(st.link(k, tid));
+            if (2 * k < 9) u[2 * k] = {v.x, v.y};
+            if (2 * k + 1 < 9) u[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    if constexpr (RECON == 12) reconstruct_row2(u);
+    Cx<float> w[2][3];
+    if constexpr (DIR > 0) su3_mul(u, h, w);
+    else su3_adj_mul(u, h, w);
+    if (!g.bc_trivial[MU] && coord_of<MU>(c) == (DIR > 0 ? g.L[MU] - 1 : 0)) boundary_phase(g, MU, DIR < 0, w, sc);
+    accumulate<MU, S>(acc, w, sc);
+}
+
+template <int P, int RECON, bool DAGGER, int NS, int J>
+__device__ __forceinline__ void staged_step(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *lo, const char *li, char *smem, int T, int tid,
+                                            Cx<float> (&acc)[12]) {
+    using L = HopLayout<P, RECON>;
+    if constexpr (J + NS - 1 < 8) {
+        Stage<P, RECON> nx{smem + ((J + NS - 1) % NS) * L::bytes * T, T};
+        stage_issue<P, RECON, J + NS - 1>(A, c, cb, in, lo, li, nx, tid);
+    }
+    cp_async_commit();
+    cp_async_wait<NS - 1>();
+    Stage<P, RECON> cur{smem + (J % NS) * L::bytes * T, T};
+    stage_compute<P, RECON, J, DAGGER>(A, c, cur, tid, acc);
+    if constexpr (J < 7) staged_step<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid, acc);
+}
+
+template <int P, int RECON, bool DAGGER, int NS, int J>
+__device__ __forceinline__ void staged_prologue(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                                const char *lo, const char *li, char *smem, int T, int tid) {
+    using L = HopLayout<P, RECON>;
+    if constexpr (J < NS - 1) {
+        Stage<P, RECON> st{smem + J * L::bytes * T, T};
+        stage_issue<P, RECON, J>(A, c, cb, in, lo, li, st, tid);
+        cp_async_commit();
+        staged_prologue<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid);
+    }
+}
+
+template <int P, int RECON, bool DAGGER, int NS>
+__device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *lo, const char *li, Cx<float> (&acc)[12]) {
+    extern __shared__ __align__(16) char smem_dyn[];
+    const int T = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    staged_prologue<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid);
+    staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc);
+}
+
+// Grid: x over the site blocks of every lattice of the batch (lattice l owns
+// blocks [block0, block0 + nblocks)), y over right-hand-side groups, z over
+// the output parities (1 or 2).  Block: (sites, right-hand sides).
+template <int P, int RECON, bool DAGGER, bool XPAY, bool RED, int NS>
+__global__ void __launch_bounds__(256, COLA_DSLASH_MINB) dslash_kernel(const __grid_constant__ DslashArgs A) {
     using R = typename Prec<P>::real;
     __shared__ double sh[32];
-    const Geom &g = A.g;
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    int l = 0;
+    while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
+    const DslashLat &L = A.lat[l];
+    const Geom &g = L.g;
+    const int cb = ((int)blockIdx.x - L.block0) * blockDim.x + threadIdx.x;
     const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
+    const int row = L.row0 + rhs;
     const int par = A.parity0 + blockIdx.z;
     const bool row_ok = rhs < A.nrhs;
     bool live = row_ok;
     if (live && A.state) {
-        const CgState &st = A.state[rhs];
+        const CgState &st = A.state[row];
         live = A.filter_ru ? (st.ru && !st.done) : !st.done;
     }
     double nrm = 0.0;
     if (cb < g.Vh && live) {
         const Coord c = cb_coord(g, cb, par);
-        const char *in = static_cast<const char *>(A.in) + rhs * A.rhs_stride + (1 - par) * A.parity_stride;
-        const char *lo = static_cast<const char *>(A.links) + par * A.link_parity_stride;
-        const char *li = static_cast<const char *>(A.links) + (1 - par) * A.link_parity_stride;
+        const char *in = static_cast<const char *>(L.in) + rhs * L.rhs_stride + (1 - par) * L.parity_stride;
+        const char *lo = static_cast<const char *>(L.links) + par * L.link_parity_stride;
+        const char *li = static_cast<const char *>(L.links) + (1 - par) * L.link_parity_stride;
         Cx<R> acc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-        hop_mu<P, RECON, 0, DAGGER>(A, c, cb, in, lo, li, acc);
-        hop_mu<P, RECON, 1, DAGGER>(A, c, cb, in, lo, li, acc);
-        hop_mu<P, RECON, 2, DAGGER>(A, c, cb, in, lo, li, acc);
-        hop_mu<P, RECON, 3, DAGGER>(A, c, cb, in, lo, li, acc);
-        const R b = (R)A.b;
+        if constexpr (NS > 0 && P != COLA_F64) {
+            hops_staged<P, RECON, DAGGER, NS>(L, c, cb, in, lo, li, acc);
+        } else {
+            hop_mu<P, RECON, 0, DAGGER>(L, c, cb, in, lo, li, acc);
+            hop_mu<P, RECON, 1, DAGGER>(L, c, cb, in, lo, li, acc);
+            hop_mu<P, RECON, 2, DAGGER>(L, c, cb, in, lo, li, acc);
+            hop_mu<P, RECON, 3, DAGGER>(L, c, cb, in, lo, li, acc);
+        }
+        const R b = (R)L.b;
         if constexpr (XPAY) {
-            const R a = (R)A.a;
+            const R a = (R)L.a;
             Cx<R> xs[12];
-            SpinorIO<P>::load(static_cast<const char *>(A.xin) + rhs * A.rhs_stride + par * A.parity_stride,
+            SpinorIO<P>::load(static_cast<const char *>(L.xin) + rhs * L.rhs_stride + par * L.parity_stride,
                               g.Vh, cb, xs);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
@@ -208,24 +413,24 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A) {
                 acc[k].im *= b;
             }
         }
-        SpinorIO<P>::store(static_cast<char *>(A.out) + rhs * A.rhs_stride + par * A.parity_stride, g.Vh, cb,
+        SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb,
                            acc);
         if constexpr (RED) {
-            R s = R(0);
+            R s2 = R(0);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) s += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
-            nrm = (double)s;
+            for (int k = 0; k < 12; ++k) s2 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
+            nrm = (double)s2;
         }
     }
     if constexpr (RED) {
-        const int nblocks = gridDim.x * gridDim.z;
-        const int bid = blockIdx.z * gridDim.x + blockIdx.x;
+        const int nblocks = L.nblocks * gridDim.z;
+        const int bid = blockIdx.z * L.nblocks + ((int)blockIdx.x - L.block0);
         double tot;
-        if (reduce_rows_last_block(nrm, A.partials, A.counters + blockIdx.y, nblocks, bid, rhs, row_ok, sh,
-                                   &tot)) {
+        if (reduce_rows_last_block(nrm, A.partials, A.pstride, row, A.counters + l * A.ngroups + blockIdx.y,
+                                   nblocks, bid, row_ok, sh, &tot)) {
             if (threadIdx.x == 0 && row_ok) {
                 if (A.state) {
-                    CgState &st = A.state[rhs];
+                    CgState &st = A.state[row];
                     if (!st.done) {
                         st.pq = tot;
                         st.rho = st.rho_new;
@@ -236,55 +441,119 @@ __global__ void __launch_bounds__(256) dslash_kernel(const DslashArgs A) {
                         }
                     }
                 } else if (A.result) {
-                    A.result[rhs] = tot;
+                    A.result[row] = tot;
                 }
             }
         }
     }
 }
 
-template <int P, int RECON, bool DAGGER, bool XPAY, bool RED>
-static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, cudaStream_t s) {
+// Pipeline depth of the staged kernels: FP16 storage moves half the bytes
+// per load of FP32, so it needs the deeper pipeline; FP32 keeps direct loads
+// (measured on GB300 at 32^3x64).  COLA_DSLASH_STAGES=0 or 3 overrides.
+static int staged_depth(int prec) {
+    static const int env_ns = [] {
+        const char *e = getenv("COLA_DSLASH_STAGES");
+        return e ? atoi(e) : -1;
+    }();
+    if (prec == COLA_F64) return 0;
+    if (env_ns >= 0) return env_ns == 0 ? 0 : 3;
+    return prec == COLA_F16 ? 3 : 0;
+}
+
+template <int P, int RECON, bool DAGGER, bool XPAY, bool RED, int NS>
+static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total_blocks, cudaStream_t s) {
     const int by = A.rhs_per_block;
     dim3 block(bx, by, 1);
-    dim3 grid((A.g.Vh + bx - 1) / bx, (A.nrhs + by - 1) / by, nparity);
-    dslash_kernel<P, RECON, DAGGER, XPAY, RED><<<grid, block, 0, s>>>(A);
+    dim3 grid(total_blocks, (A.nrhs + by - 1) / by, nparity);
+    size_t smem = 0;
+    if constexpr (NS > 0 && P != COLA_F64) {
+        smem = (size_t)NS * HopLayout<P, RECON>::bytes * bx * by;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(dslash_kernel<P, RECON, DAGGER, XPAY, RED, NS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr_set = true;
+        }
+    }
+    dslash_kernel<P, RECON, DAGGER, XPAY, RED, NS><<<grid, block, smem, s>>>(A);
     return cudaGetLastError();
 }
 
+template <int P, int RECON, bool DAGGER, bool XPAY, bool RED>
+static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cudaStream_t s) {
+    if constexpr (P == COLA_F64) {
+        return launch_ns<P, RECON, DAGGER, XPAY, RED, 0>(A, nparity, bx, nb, s);
+    } else {
+        if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, XPAY, RED, 0>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, XPAY, RED, 3>(A, nparity, bx, nb, s);
+    }
+}
+
 template <int P, int RECON>
-static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, bool xpay, bool red, int bx,
+static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, bool xpay, bool red, int bx, int nb,
                             cudaStream_t s) {
     if (dagger) {
-        if (xpay) return red ? launch_t<P, RECON, true, true, true>(A, nparity, bx, s)
-                             : launch_t<P, RECON, true, true, false>(A, nparity, bx, s);
-        return red ? launch_t<P, RECON, true, false, true>(A, nparity, bx, s)
-                   : launch_t<P, RECON, true, false, false>(A, nparity, bx, s);
+        if (xpay) return red ? launch_t<P, RECON, true, true, true>(A, nparity, bx, nb, s)
+                             : launch_t<P, RECON, true, true, false>(A, nparity, bx, nb, s);
+        return red ? launch_t<P, RECON, true, false, true>(A, nparity, bx, nb, s)
+                   : launch_t<P, RECON, true, false, false>(A, nparity, bx, nb, s);
     }
-    if (xpay) return red ? launch_t<P, RECON, false, true, true>(A, nparity, bx, s)
-                         : launch_t<P, RECON, false, true, false>(A, nparity, bx, s);
-    return red ? launch_t<P, RECON, false, false, true>(A, nparity, bx, s)
-               : launch_t<P, RECON, false, false, false>(A, nparity, bx, s);
+    if (xpay) return red ? launch_t<P, RECON, false, true, true>(A, nparity, bx, nb, s)
+                         : launch_t<P, RECON, false, true, false>(A, nparity, bx, nb, s);
+    return red ? launch_t<P, RECON, false, false, true>(A, nparity, bx, nb, s)
+               : launch_t<P, RECON, false, false, false>(A, nparity, bx, nb, s);
 }
 
-cudaError_t launch_dslash(int prec, int recon, const DslashArgs &A, int nparity, bool dagger, bool xpay,
-                          bool red, int block_x, cudaStream_t s) {
+// Site blocks per lattice for block_x; returns the total.
+static int assign_blocks(DslashArgs &A, int bx) {
+    int total = 0;
+    for (int l = 0; l < A.nlat; ++l) {
+        A.lat[l].block0 = total;
+        A.lat[l].nblocks = (A.lat[l].g.Vh + bx - 1) / bx;
+        total += A.lat[l].nblocks;
+    }
+    return total;
+}
+
+void dslash_reduce_shape(const DslashArgs &A, int nparity, int block_x, int *pstride, int *ncounters) {
+    const int bx = block_x > 0 ? block_x : default_dslash_block(0, A.rhs_per_block);
+    int mx = 0;
+    for (int l = 0; l < A.nlat; ++l) {
+        const int nb = (A.lat[l].g.Vh + bx - 1) / bx;
+        if (nb > mx) mx = nb;
+    }
+    *pstride = mx * nparity;
+    *ncounters = A.nlat * ((A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block);
+}
+
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+                          int block_x, cudaStream_t s) {
     if (block_x <= 0) block_x = default_dslash_block(prec, A.rhs_per_block);
+    if (A.nlat < 1 || A.nlat > kMaxBatch) return cudaErrorInvalidValue;
+    const int nb = assign_blocks(A, block_x);
+    A.ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
     switch (prec) {
         case COLA_F64:
-            return recon == 12 ? launch_r<COLA_F64, 12>(A, nparity, dagger, xpay, red, block_x, s)
-                               : launch_r<COLA_F64, 18>(A, nparity, dagger, xpay, red, block_x, s);
+            return recon == 12 ? launch_r<COLA_F64, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
+                               : launch_r<COLA_F64, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
         case COLA_F32:
-            return recon == 12 ? launch_r<COLA_F32, 12>(A, nparity, dagger, xpay, red, block_x, s)
-                               : launch_r<COLA_F32, 18>(A, nparity, dagger, xpay, red, block_x, s);
+            return recon == 12 ? launch_r<COLA_F32, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
+                               : launch_r<COLA_F32, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
         default:
-            return recon == 12 ? launch_r<COLA_F16, 12>(A, nparity, dagger, xpay, red, block_x, s)
-                               : launch_r<COLA_F16, 18>(A, nparity, dagger, xpay, red, block_x, s);
+            return recon == 12 ? launch_r<COLA_F16, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
+                               : launch_r<COLA_F16, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
     }
 }
 
+// Threads per block along the sites; COLA_DSLASH_BLOCK overrides (tuning runs).
 int default_dslash_block(int prec, int rhs_per_block) {
-    int bx = prec == COLA_F64 ? 128 : 128;
+    static const int env_bx = [] {
+        const char *e = getenv("COLA_DSLASH_BLOCK");
+        int v = e ? atoi(e) : 0;
+        return (v >= 32 && v <= 1024 && v % 32 == 0) ? v : 0;
+    }();
+    int bx = env_bx ? env_bx : 128;
     while (bx * rhs_per_block > 256 && bx > 32) bx >>= 1;
     return bx;
 }

@@ -20,8 +20,12 @@
 // loop: a host loop that reads the per-right-hand-side state after each
 // update, or one CUDA graph whose while/if conditional nodes are set by a
 // one-thread control kernel, so that a whole solve is a single launch.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
+#include <initializer_list>
+#include <utility>
 #include <vector>
 
 #include "cola_impl.h"
@@ -53,88 +57,135 @@ namespace {
 enum Slot {
     S_T = 0, S_MP = 1,              // low-precision temporaries of the operator
     S_P = 2, S_Q = 3, S_RLO = 4, S_XLO = 5,
-    S_B = 6, S_XHI = 7, S_RHI = 8, S_AX = 9, S_T64 = 10, S_MP64 = 11, S_BORIG = 12,
+    S_B = 6, S_XHI = 7, S_RHI = 8, S_AX = 9, S_T64 = 10, S_MP64 = 11, S_BORIG = 12, S_NORMS = 13,
+};
+
+// Vectors of one lattice of the batch (full packed fields x nrhs, held in
+// that lattice's gauge-handle workspace).
+struct LatCtx {
+    cola_gauge g;
+    int row0;
+    void *t, *mp, *p, *q, *rlo, *xlo;
+    void *b, *xhi, *rhi, *ax, *t64, *mp64, *borig;
 };
 
 struct SolveCtx {
-    cola_gauge g;
+    int nlat;
+    LatCtx lat[kMaxBatch];
+    cola_gauge owner;  // holds states and reduction scratch
     int prec, xprec, op, nrhs, nparity;
-    void *t, *mp, *p, *q, *rlo, *xlo;
-    void *b, *xhi, *rhi, *ax, *t64, *mp64, *borig;
-    size_t lo_bytes, x_bytes, hi_bytes;
-    BlasDims dims;
 };
 
-VecRef vref(void *p, int prec, const Geom &g) {
-    VecRef v;
-    v.ptr = p;
-    v.prec = prec;
-    v.parity_stride = spinor_parity_bytes(prec, g.Vh);
-    v.rhs_stride = 2 * v.parity_stride;
-    return v;
+enum VecId { V_T, V_MP, V_P, V_Q, V_RLO, V_XLO, V_B, V_XHI, V_RHI, V_AX, V_T64, V_MP64, V_BORIG };
+
+void *vec(const LatCtx &L, VecId v) {
+    switch (v) {
+        case V_T: return L.t;
+        case V_MP: return L.mp;
+        case V_P: return L.p;
+        case V_Q: return L.q;
+        case V_RLO: return L.rlo;
+        case V_XLO: return L.xlo;
+        case V_B: return L.b;
+        case V_XHI: return L.xhi;
+        case V_RHI: return L.rhi;
+        case V_AX: return L.ax;
+        case V_T64: return L.t64;
+        case V_MP64: return L.mp64;
+        default: return L.borig;
+    }
 }
 
-cola_status ru_block(SolveCtx &c, cudaStream_t s) {
-    const Geom &G = c.g->geom;
-    COLA_CUDA(launch_ru_accumulate(c.dims, vref(c.xhi, COLA_F64, G), vref(c.xlo, c.xprec, G), c.g->states, false, s),
-              "reliable update (accumulate)");
-    COLA_TRY(apply_mdagm(c.g, COLA_F64, c.op, c.ax, c.xhi, c.t64, c.mp64, c.nrhs, c.g->states, true, false, s));
-    COLA_CUDA(launch_ru_residual(c.dims, vref(c.rhi, COLA_F64, G), vref(c.b, COLA_F64, G), vref(c.ax, COLA_F64, G),
-                                 vref(c.rlo, c.prec, G), vref(c.p, c.prec, G), c.g->states, false, false,
-                                 c.g->partials, c.g->counters, s),
-              "reliable update (residual)");
+// Batched vector-kernel arguments over every lattice, slots from `ids`.
+BlasArgs blas(const SolveCtx &c, std::initializer_list<std::pair<VecId, int>> ids, int nparity = -1) {
+    BlasArgs B;
+    std::memset(&B, 0, sizeof(B));
+    B.nlat = c.nlat;
+    B.nparity = nparity < 0 ? c.nparity : nparity;
+    B.nrhs = c.nrhs;
+    int k = 0;
+    for (auto &id : ids) B.prec[k++] = id.second;
+    for (int l = 0; l < c.nlat; ++l) {
+        B.lat[l].vh = c.lat[l].g->geom.Vh;
+        B.lat[l].row0 = c.lat[l].row0;
+        k = 0;
+        for (auto &id : ids) B.lat[l].v[k++] = vec(c.lat[l], id.first);
+    }
+    B.state = c.owner->states;
+    B.partials = c.owner->partials;
+    B.pstride = blas_pstride(B);
+    B.counters = c.owner->counters;
+    return B;
+}
+
+cola_status mdagm(const SolveCtx &c, int prec, VecId out, VecId in, VecId t, VecId mp, CgState *st, bool filter_ru,
+                  bool reduce, cudaStream_t s) {
+    OpLat L[kMaxBatch];
+    for (int l = 0; l < c.nlat; ++l)
+        L[l] = {c.lat[l].g, vec(c.lat[l], out), vec(c.lat[l], in), vec(c.lat[l], t), vec(c.lat[l], mp), c.lat[l].row0};
+    return apply_mdagm_batch(c.nlat, L, prec, c.op, c.nrhs, st, filter_ru, reduce, s);
+}
+
+cola_status ru_block(const SolveCtx &c, cudaStream_t s) {
+    BlasArgs B = blas(c, {{V_XHI, COLA_F64}, {V_XLO, c.xprec}});
+    COLA_CUDA(launch_ru_accumulate(B, false, s), "reliable update (accumulate)");
+    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, c.owner->states, true, false, s));
+    B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
+    COLA_CUDA(launch_ru_residual(B, s), "reliable update (residual)");
     return COLA_OK;
 }
 
-cola_status iter_head(SolveCtx &c, cudaStream_t s) {
-    const Geom &G = c.g->geom;
-    COLA_TRY(apply_mdagm(c.g, c.prec, c.op, c.q, c.p, c.t, c.mp, c.nrhs, c.g->states, false, true, s));
-    COLA_CUDA(launch_cg_update_xr(c.dims, vref(c.xlo, c.xprec, G), vref(c.rlo, c.prec, G), vref(c.p, c.prec, G),
-                                  vref(c.q, c.prec, G), c.g->states, c.g->partials, c.g->counters, s),
-              "cg update x, r");
+cola_status iter_head(const SolveCtx &c, cudaStream_t s) {
+    COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, true, s));
+    BlasArgs B = blas(c, {{V_XLO, c.xprec}, {V_RLO, c.prec}, {V_P, c.prec}, {V_Q, c.prec}});
+    COLA_CUDA(launch_cg_update_xr(B, s), "cg update x, r");
     return COLA_OK;
 }
 
-cola_status iter_tail(SolveCtx &c, cudaStream_t s) {
-    const Geom &G = c.g->geom;
-    COLA_CUDA(launch_cg_update_p(c.dims, vref(c.p, c.prec, G), vref(c.rlo, c.prec, G), c.g->states, false, s),
-              "cg update p");
+cola_status iter_tail(const SolveCtx &c, cudaStream_t s) {
+    BlasArgs B = blas(c, {{V_P, c.prec}, {V_RLO, c.prec}});
+    COLA_CUDA(launch_cg_update_p(B, s), "cg update p");
     return COLA_OK;
 }
 
-cola_status read_states(SolveCtx &c, cudaStream_t s) {
-    COLA_CUDA(cudaMemcpyAsync(c.g->h_states, c.g->states, c.nrhs * sizeof(CgState), cudaMemcpyDeviceToHost, s),
+int total_rows(const SolveCtx &c) { return c.nlat * c.nrhs; }
+
+cola_status read_states(const SolveCtx &c, cudaStream_t s) {
+    COLA_CUDA(cudaMemcpyAsync(c.owner->h_states, c.owner->states, total_rows(c) * sizeof(CgState),
+                              cudaMemcpyDeviceToHost, s),
               "state readback");
     COLA_CUDA(cudaStreamSynchronize(s), "solver synchronisation");
     return COLA_OK;
 }
 
 // Host-driven loop: one state readback per iteration.
-cola_status run_host_loop(SolveCtx &c, cudaStream_t s) {
+cola_status run_host_loop(const SolveCtx &c, cudaStream_t s) {
     for (;;) {
         COLA_TRY(iter_head(c, s));
         COLA_TRY(read_states(c, s));
         bool any_ru = false, running = false;
-        for (int r = 0; r < c.nrhs; ++r) {
-            const CgState &st = c.g->h_states[r];
+        for (int r = 0; r < total_rows(c); ++r) {
+            const CgState &st = c.owner->h_states[r];
             any_ru |= st.ru && !st.done;
         }
         if (any_ru) {
             COLA_TRY(ru_block(c, s));
             COLA_TRY(read_states(c, s));
         }
-        for (int r = 0; r < c.nrhs; ++r) running |= !c.g->h_states[r].done;
+        for (int r = 0; r < total_rows(c); ++r) running |= !c.owner->h_states[r].done;
         if (!running) return COLA_OK;
         COLA_TRY(iter_tail(c, s));
     }
 }
 
 // Whole loop as one graph: while (running) { head; if (ru) { ru_block } ; tail }.
-cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
+cola_status run_graph_loop(const SolveCtx &c, cudaStream_t s) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
     cola_status st = COLA_OK;
+    const int nrows = total_rows(c);
+    CgState *states = c.owner->states;
     auto fail = [&](cola_status e) {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -156,7 +207,6 @@ cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     if ((st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream")) != COLA_OK)
         return fail(st);
-    // body part 1: iteration head, then the control kernel for the "if"
     if ((st = cuda_check(cudaGraphConditionalHandleCreate(&h_ru, body, 0, cudaGraphCondAssignDefault),
                          "graph conditional")) != COLA_OK)
         return fail(st);
@@ -165,10 +215,9 @@ cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
         return fail(st);
     st = iter_head(c, cs);
     if (st == COLA_OK) {
-        control_ru_kernel<<<1, 1, 0, cs>>>(c.g->states, c.nrhs, h_ru);
+        control_ru_kernel<<<1, 1, 0, cs>>>(states, nrows, h_ru);
         st = cuda_check(cudaGetLastError(), "control kernel");
     }
-    // if node appended to the capture
     cudaGraphNode_t ifnode = nullptr;
     cudaGraph_t ifbody = nullptr;
     if (st == COLA_OK) {
@@ -194,7 +243,7 @@ cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
     }
     if (st == COLA_OK) st = iter_tail(c, cs);
     if (st == COLA_OK) {
-        control_loop_kernel<<<1, 1, 0, cs>>>(c.g->states, c.nrhs, h_loop);
+        control_loop_kernel<<<1, 1, 0, cs>>>(states, nrows, h_loop);
         st = cuda_check(cudaGetLastError(), "control kernel");
     }
     {
@@ -203,7 +252,6 @@ cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
         if (st == COLA_OK) st = cuda_check(e, "end capture");
     }
     if (st != COLA_OK) return fail(st);
-    // the "if" body: the FP64 reliable update
     if ((st = cuda_check(cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0,
                                                        cudaStreamCaptureModeThreadLocal),
                          "capture")) != COLA_OK)
@@ -222,21 +270,12 @@ cola_status run_graph_loop(SolveCtx &c, cudaStream_t s) {
     return read_states(c, s);
 }
 
-}  // namespace
-
-static cola_status arg_error(const char *msg) {
+cola_status arg_error(const char *msg) {
     set_error(msg);
     return COLA_ERR_ARG;
 }
 
-}  // namespace cola
-
-using namespace cola;
-
-extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev, const cola_solver_params *prm,
-                                     cola_solve_info *info, cudaStream_t s) {
-    const auto t0 = std::chrono::steady_clock::now();
-    if (!g || !x_dev || !b_dev || !prm || !info) return arg_error("null argument to cola_cg_solve");
+cola_status check_params(const cola_solver_params *prm) {
     if (prm->op != COLA_OP_FULL && prm->op != COLA_OP_EO) return arg_error("op must be COLA_OP_FULL or COLA_OP_EO");
     if (prm->system != COLA_SYS_NORMAL && prm->system != COLA_SYS_DIRAC)
         return arg_error("system must be COLA_SYS_NORMAL or COLA_SYS_DIRAC");
@@ -245,144 +284,185 @@ extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_de
     if (!(prm->tol > 0.0) || prm->max_iter < 0) return arg_error("tol must be > 0 and max_iter >= 0");
     if (prm->inner != COLA_F64 && !(prm->delta > 0.0 && prm->delta < 1.0))
         return arg_error("delta must be in (0, 1) for a mixed-precision solve");
-    if (!g->links[COLA_F64]) {
-        set_error("cola_cg_solve needs FP64 links in the gauge handle (reliable updates and residuals)");
-        return COLA_ERR_UNSUPPORTED;
-    }
-    if (!g->links[prm->inner]) {
-        set_error("gauge handle holds no links of the inner precision");
-        return COLA_ERR_UNSUPPORTED;
-    }
-    const Geom &G = g->geom;
+    return COLA_OK;
+}
+
+// Solve every lattice of the batch together: one launch per kernel per
+// iteration covers all lattices and right-hand sides.
+cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const void *const *bs,
+                        const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    COLA_TRY(check_params(prm));
     SolveCtx c;
-    c.g = g;
+    std::memset(&c, 0, sizeof(c));
+    c.nlat = nlat;
+    c.owner = gs[0];
     c.prec = prm->inner;
     c.xprec = prm->inner == COLA_F64 ? COLA_F64 : COLA_F32;
     c.op = prm->op;
     c.nrhs = prm->nrhs;
     c.nparity = prm->op == COLA_OP_EO ? 1 : 2;
-    c.dims = {G.Vh, c.nparity, c.nrhs};
-    c.lo_bytes = 2 * spinor_parity_bytes(c.prec, G.Vh) * c.nrhs;
-    c.x_bytes = 2 * spinor_parity_bytes(c.xprec, G.Vh) * c.nrhs;
-    c.hi_bytes = 2 * spinor_parity_bytes(COLA_F64, G.Vh) * c.nrhs;
-    COLA_TRY(ws_slot(g, S_T, c.lo_bytes, &c.t));
-    COLA_TRY(ws_slot(g, S_MP, c.lo_bytes, &c.mp));
-    COLA_TRY(ws_slot(g, S_P, c.lo_bytes, &c.p));
-    COLA_TRY(ws_slot(g, S_Q, c.lo_bytes, &c.q));
-    COLA_TRY(ws_slot(g, S_RLO, c.lo_bytes, &c.rlo));
-    COLA_TRY(ws_slot(g, S_XLO, c.x_bytes, &c.xlo));
-    COLA_TRY(ws_slot(g, S_B, c.hi_bytes, &c.b));
-    COLA_TRY(ws_slot(g, S_XHI, c.hi_bytes, &c.xhi));
-    COLA_TRY(ws_slot(g, S_RHI, c.hi_bytes, &c.rhi));
-    COLA_TRY(ws_slot(g, S_AX, c.hi_bytes, &c.ax));
-    COLA_TRY(ws_slot(g, S_T64, c.hi_bytes, &c.t64));
-    COLA_TRY(ws_slot(g, S_MP64, c.hi_bytes, &c.mp64));
-    c.borig = nullptr;
-    if (prm->system == COLA_SYS_DIRAC) COLA_TRY(ws_slot(g, S_BORIG, c.hi_bytes, &c.borig));
-    // reduction scratch sized for the largest launch of this solve
-    {
-        const size_t blas_blocks = (size_t)(G.Vh * 2 + 255) / 256;
-        const size_t ds_blocks = (size_t)((G.Vh + 31) / 32) * 2;
-        COLA_TRY(ws_reduce(g, c.nrhs, blas_blocks > ds_blocks ? blas_blocks : ds_blocks));
-    }
-    COLA_TRY(ws_states(g, c.nrhs));
-
-    const double k = g->lat.kappa;
-    const int pmask_b = (prm->op == COLA_OP_EO && prm->system == COLA_SYS_NORMAL) ? 1 : 3;
-    // right-hand side of the CG system in b (packed FP64)
-    if (prm->system == COLA_SYS_NORMAL) {
-        COLA_CUDA(launch_pack_spinor(COLA_F64, G, c.b, b_dev, c.nrhs, pmask_b, s), "pack b");
-    } else {
-        COLA_CUDA(launch_pack_spinor(COLA_F64, G, c.borig, b_dev, c.nrhs, 3, s), "pack b");
-        if (prm->op == COLA_OP_EO) {
-            // bhat_e = b_e + kappa H_eo b_o (into mp64);  b = Mhat^dag bhat
-            DslashArgs A = make_dslash_args(g, COLA_F64, c.mp64, c.borig, c.borig, c.nrhs, 0, 1.0, k);
-            COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 1, false, true, false, 0, s), "source prep");
-            A = make_dslash_args(g, COLA_F64, c.t64, c.mp64, nullptr, c.nrhs, 1, 0.0, 1.0);
-            COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 1, true, false, false, 0, s), "source prep");
-            A = make_dslash_args(g, COLA_F64, c.b, c.t64, c.mp64, c.nrhs, 0, 1.0, -k * k);
-            COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 1, true, true, false, 0, s), "source prep");
-        } else {
-            // b = D^dag b
-            DslashArgs A = make_dslash_args(g, COLA_F64, c.b, c.borig, c.borig, c.nrhs, 0, 1.0, -k);
-            COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 2, true, true, false, 0, s), "source prep");
+    const bool dirac = prm->system == COLA_SYS_DIRAC;
+    int pstride = 0, nrows = nlat * c.nrhs;
+    for (int l = 0; l < nlat; ++l) {
+        cola_gauge g = gs[l];
+        if (!g->links[COLA_F64]) {
+            set_error("cola_cg_solve needs FP64 links in every gauge handle (reliable updates and residuals)");
+            return COLA_ERR_UNSUPPORTED;
         }
+        if (!g->links[c.prec]) {
+            set_error("a gauge handle holds no links of the inner precision");
+            return COLA_ERR_UNSUPPORTED;
+        }
+        if (g->recon[COLA_F64] != gs[0]->recon[COLA_F64] || g->recon[c.prec] != gs[0]->recon[c.prec])
+            return arg_error("the gauge handles of a batch must use the same link reconstruction per precision");
+        for (int m = 0; m < l; ++m)
+            if (gs[m] == g) return arg_error("a gauge handle appears twice in the batch (use nrhs instead)");
+        const Geom &G = g->geom;
+        LatCtx &L = c.lat[l];
+        L.g = g;
+        L.row0 = l * c.nrhs;
+        const size_t lo = 2 * spinor_parity_bytes(c.prec, G.Vh) * c.nrhs;
+        const size_t xb = 2 * spinor_parity_bytes(c.xprec, G.Vh) * c.nrhs;
+        const size_t hi = 2 * spinor_parity_bytes(COLA_F64, G.Vh) * c.nrhs;
+        COLA_TRY(ws_slot(g, S_T, lo, &L.t));
+        COLA_TRY(ws_slot(g, S_MP, lo, &L.mp));
+        COLA_TRY(ws_slot(g, S_P, lo, &L.p));
+        COLA_TRY(ws_slot(g, S_Q, lo, &L.q));
+        COLA_TRY(ws_slot(g, S_RLO, lo, &L.rlo));
+        COLA_TRY(ws_slot(g, S_XLO, xb, &L.xlo));
+        COLA_TRY(ws_slot(g, S_B, hi, &L.b));
+        COLA_TRY(ws_slot(g, S_XHI, hi, &L.xhi));
+        COLA_TRY(ws_slot(g, S_RHI, hi, &L.rhi));
+        COLA_TRY(ws_slot(g, S_AX, hi, &L.ax));
+        COLA_TRY(ws_slot(g, S_T64, hi, &L.t64));
+        COLA_TRY(ws_slot(g, S_MP64, hi, &L.mp64));
+        L.borig = nullptr;
+        if (dirac) COLA_TRY(ws_slot(g, S_BORIG, hi, &L.borig));
+        const int blas_blocks = (G.Vh * 2 + 255) / 256;
+        const int ds_blocks = ((G.Vh + 31) / 32) * 2;
+        pstride = std::max(pstride, std::max(blas_blocks, ds_blocks));
     }
-    COLA_CUDA(launch_pack_spinor(COLA_F64, G, c.xhi, x_dev, c.nrhs, prm->op == COLA_OP_EO ? 1 : 3, s), "pack x0");
-    COLA_CUDA(cudaMemsetAsync(c.xlo, 0, c.x_bytes, s), "zero x_lo");
+    COLA_TRY(ws_reduce(c.owner, nrows, pstride, (size_t)nrows * 2));
+    COLA_TRY(ws_states(c.owner, nrows));
+    CgState *hs = c.owner->h_states;
 
-    // per right-hand side state
-    for (int r = 0; r < c.nrhs; ++r) {
-        CgState &st = g->h_states[r];
+    // right-hand side of the CG system in b (packed FP64), initial guess in x_hi
+    for (int l = 0; l < nlat; ++l) {
+        LatCtx &L = c.lat[l];
+        cola_gauge g = L.g;
+        const Geom &G = g->geom;
+        const double k = g->lat.kappa;
+        if (!dirac) {
+            const int pmask = prm->op == COLA_OP_EO ? 1 : 3;
+            COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.b, bs[l], c.nrhs, pmask, s), "pack b");
+        } else {
+            COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.borig, bs[l], c.nrhs, 3, s), "pack b");
+            if (prm->op == COLA_OP_EO) {
+                // bhat_e = b_e + kappa H_eo b_o (into mp64);  b = Mhat^dag bhat
+                DslashArgs A = make_dslash_args(g, COLA_F64, L.mp64, L.borig, L.borig, c.nrhs, 0, 1.0, k);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, false, s));
+                A = make_dslash_args(g, COLA_F64, L.t64, L.mp64, nullptr, c.nrhs, 1, 0.0, 1.0);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, false, false, s));
+                A = make_dslash_args(g, COLA_F64, L.b, L.t64, L.mp64, c.nrhs, 0, 1.0, -k * k);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, true, false, s));
+            } else {
+                DslashArgs A = make_dslash_args(g, COLA_F64, L.b, L.borig, L.borig, c.nrhs, 0, 1.0, -k);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 2, true, true, false, s));
+            }
+        }
+        COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.xhi, xs[l], c.nrhs, prm->op == COLA_OP_EO ? 1 : 3, s), "pack x0");
+        COLA_CUDA(cudaMemsetAsync(L.xlo, 0, 2 * spinor_parity_bytes(c.xprec, G.Vh) * c.nrhs, s), "zero x_lo");
+    }
+    for (int r = 0; r < nrows; ++r) {
+        CgState &st = hs[r];
         std::memset(&st, 0, sizeof(st));
         st.tol2 = prm->tol * prm->tol;
         st.delta2 = prm->inner == COLA_F64 ? 0.0 : prm->delta * prm->delta;
         st.max_iter = prm->max_iter;
         st.status = COLA_ERR_NOT_CONVERGED;
     }
-    COLA_CUDA(cudaMemcpyAsync(g->states, g->h_states, c.nrhs * sizeof(CgState), cudaMemcpyHostToDevice, s),
+    COLA_CUDA(cudaMemcpyAsync(c.owner->states, hs, nrows * sizeof(CgState), cudaMemcpyHostToDevice, s),
               "state upload");
-    COLA_CUDA(launch_init_norms(c.dims, vref(c.b, COLA_F64, G), g->states, g->partials, g->counters, s), "|b|^2");
+    {
+        BlasArgs B = blas(c, {{V_B, COLA_F64}});
+        COLA_CUDA(launch_init_norms(B, s), "|b|^2");
+    }
     // r = b - A x0 in FP64, r_lo = p = r
-    COLA_TRY(apply_mdagm(g, COLA_F64, c.op, c.ax, c.xhi, c.t64, c.mp64, c.nrhs, nullptr, false, false, s));
-    COLA_CUDA(launch_ru_residual(c.dims, vref(c.rhi, COLA_F64, G), vref(c.b, COLA_F64, G), vref(c.ax, COLA_F64, G),
-                                 vref(c.rlo, c.prec, G), vref(c.p, c.prec, G), g->states, true, true, g->partials,
-                                 g->counters, s),
-              "initial residual");
+    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, false, s));
+    {
+        BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
+        B.init = 1;
+        COLA_CUDA(launch_ru_residual(B, s), "initial residual");
+    }
     COLA_TRY(read_states(c, s));
     bool running = false;
-    for (int r = 0; r < c.nrhs; ++r) {
-        running |= !g->h_states[r].done;
-        if (g->h_states[r].b2 == 0.0)  // b = 0: the solution is x = 0 whatever the guess
-            COLA_CUDA(cudaMemsetAsync(static_cast<char *>(c.xhi) + r * (c.hi_bytes / c.nrhs), 0, c.hi_bytes / c.nrhs, s),
-                      "zero x");
+    for (int l = 0; l < nlat; ++l) {
+        const size_t hi1 = 2 * spinor_parity_bytes(COLA_F64, c.lat[l].g->geom.Vh);
+        for (int r = 0; r < c.nrhs; ++r) {
+            const CgState &st = hs[c.lat[l].row0 + r];
+            running |= !st.done;
+            if (st.b2 == 0.0)  // b = 0: the solution is x = 0 whatever the guess
+                COLA_CUDA(cudaMemsetAsync(static_cast<char *>(c.lat[l].xhi) + r * hi1, 0, hi1, s), "zero x");
+        }
     }
     if (running) COLA_TRY(prm->use_graph ? run_graph_loop(c, s) : run_host_loop(c, s));
-    // a row stopped by breakdown may still hold work in x_lo
-    COLA_CUDA(launch_ru_accumulate(c.dims, vref(c.xhi, COLA_F64, G), vref(c.xlo, c.xprec, G), g->states, true, s),
-              "final accumulate");
-
-    if (prm->system == COLA_SYS_DIRAC && prm->op == COLA_OP_EO) {
-        // x_o = b_o + kappa H_oe x_e
-        DslashArgs A = make_dslash_args(g, COLA_F64, c.xhi, c.xhi, c.borig, c.nrhs, 1, 1.0, k);
-        COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 1, false, true, false, 0, s), "odd reconstruction");
+    {
+        // a row stopped by breakdown may still hold work in x_lo
+        BlasArgs B = blas(c, {{V_XHI, COLA_F64}, {V_XLO, c.xprec}});
+        COLA_CUDA(launch_ru_accumulate(B, true, s), "final accumulate");
     }
-    if (prm->op == COLA_OP_EO && prm->system == COLA_SYS_NORMAL) {
-        const size_t pb = spinor_parity_bytes(COLA_F64, G.Vh);
-        for (int r = 0; r < c.nrhs; ++r)
-            COLA_CUDA(cudaMemsetAsync(static_cast<char *>(c.xhi) + (2 * r + 1) * pb, 0, pb, s), "zero odd x");
+    std::vector<double> dirac_res(nrows, -1.0);
+    for (int l = 0; l < nlat; ++l) {
+        LatCtx &L = c.lat[l];
+        cola_gauge g = L.g;
+        const Geom &G = g->geom;
+        const double k = g->lat.kappa;
+        if (dirac && prm->op == COLA_OP_EO) {
+            // x_o = b_o + kappa H_oe x_e
+            DslashArgs A = make_dslash_args(g, COLA_F64, L.xhi, L.xhi, L.borig, c.nrhs, 1, 1.0, k);
+            COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, false, s));
+        }
+        if (prm->op == COLA_OP_EO && !dirac) {
+            const size_t pb = spinor_parity_bytes(COLA_F64, G.Vh);
+            for (int r = 0; r < c.nrhs; ++r)
+                COLA_CUDA(cudaMemsetAsync(static_cast<char *>(L.xhi) + (2 * r + 1) * pb, 0, pb, s), "zero odd x");
+        }
+        COLA_CUDA(launch_unpack_spinor(COLA_F64, G, xs[l], L.xhi, c.nrhs, 3, s), "unpack x");
     }
-    COLA_CUDA(launch_unpack_spinor(COLA_F64, G, x_dev, c.xhi, c.nrhs, 3, s), "unpack x");
-    std::vector<double> dirac_res(c.nrhs, -1.0);
-    if (prm->system == COLA_SYS_DIRAC) {
-        // |b - D x| / |b| on the whole lattice
-        const BlasDims full = {G.Vh, 2, c.nrhs};
-        DslashArgs A = make_dslash_args(g, COLA_F64, c.ax, c.xhi, c.xhi, c.nrhs, 0, 1.0, -k);
-        COLA_CUDA(launch_dslash(COLA_F64, g->recon[COLA_F64], A, 2, false, true, false, 0, s), "D x");
-        COLA_CUDA(launch_axpby(full, vref(c.rhi, COLA_F64, G), 1.0, vref(c.borig, COLA_F64, G), -1.0,
-                               vref(c.ax, COLA_F64, G), s),
-                  "b - D x");
+    if (dirac) {
+        // |b - D x| / |b| on the whole lattice, every lattice
+        for (int l = 0; l < nlat; ++l) {
+            LatCtx &L = c.lat[l];
+            DslashArgs A = make_dslash_args(L.g, COLA_F64, L.ax, L.xhi, L.xhi, c.nrhs, 0, 1.0, -L.g->lat.kappa);
+            COLA_TRY(dslash_launch(L.g, COLA_F64, A, 2, false, true, false, s));
+        }
         double *d_norms;
-        COLA_TRY(ws_slot(g, 13, 2 * c.nrhs * sizeof(double), reinterpret_cast<void **>(&d_norms)));
-        COLA_CUDA(launch_norm2(full, vref(c.rhi, COLA_F64, G), d_norms, g->partials, g->counters, s), "norm");
-        COLA_CUDA(launch_norm2(full, vref(c.borig, COLA_F64, G), d_norms + c.nrhs, g->partials, g->counters, s),
-                  "norm");
-        std::vector<double> h(2 * c.nrhs);
-        COLA_CUDA(cudaMemcpyAsync(h.data(), d_norms, 2 * c.nrhs * sizeof(double), cudaMemcpyDeviceToHost, s),
+        COLA_TRY(ws_slot(c.owner, S_NORMS, 2 * nrows * sizeof(double), reinterpret_cast<void **>(&d_norms)));
+        BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_BORIG, COLA_F64}, {V_AX, COLA_F64}}, 2);
+        B.a = 1.0;
+        B.b = -1.0;
+        COLA_CUDA(launch_axpby(B, s), "b - D x");
+        B = blas(c, {{V_RHI, COLA_F64}}, 2);
+        B.out = d_norms;
+        COLA_CUDA(launch_norm2(B, s), "norm");
+        B = blas(c, {{V_BORIG, COLA_F64}}, 2);
+        B.out = d_norms + nrows;
+        COLA_CUDA(launch_norm2(B, s), "norm");
+        std::vector<double> h(2 * nrows);
+        COLA_CUDA(cudaMemcpyAsync(h.data(), d_norms, 2 * nrows * sizeof(double), cudaMemcpyDeviceToHost, s),
                   "norm readback");
         COLA_CUDA(cudaStreamSynchronize(s), "sync");
-        for (int r = 0; r < c.nrhs; ++r) dirac_res[r] = h[c.nrhs + r] > 0 ? std::sqrt(h[r] / h[c.nrhs + r]) : 0.0;
+        for (int r = 0; r < nrows; ++r) dirac_res[r] = h[nrows + r] > 0 ? std::sqrt(h[r] / h[nrows + r]) : 0.0;
     }
     COLA_TRY(read_states(c, s));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     cola_status worst = COLA_OK;
-    for (int r = 0; r < c.nrhs; ++r) {
-        const CgState &st = g->h_states[r];
+    for (int r = 0; r < nrows; ++r) {
+        const CgState &st = hs[r];
         info[r].iters = st.iter;
         info[r].reliable_updates = st.ru_count;
-        info[r].true_rel_resid = prm->system == COLA_SYS_DIRAC ? dirac_res[r]
-                                 : st.b2 > 0                   ? std::sqrt(st.r2_last / st.b2)
-                                                               : 0.0;
+        info[r].true_rel_resid = dirac ? dirac_res[r] : st.b2 > 0 ? std::sqrt(st.r2_last / st.b2) : 0.0;
         info[r].seconds = secs;
         info[r].status = st.status;
         if (st.status != COLA_OK && worst == COLA_OK) worst = (cola_status)st.status;
@@ -390,4 +470,26 @@ extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_de
     if (worst != COLA_OK) set_error(worst == COLA_ERR_BREAKDOWN ? "CG breakdown (non-finite or non-positive scalar)"
                                                                 : "CG did not converge within max_iter");
     return worst;
+}
+
+}  // namespace
+
+}  // namespace cola
+
+using namespace cola;
+
+extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev, const cola_solver_params *prm,
+                                     cola_solve_info *info, cudaStream_t s) {
+    if (!g || !x_dev || !b_dev || !prm || !info) return arg_error("null argument to cola_cg_solve");
+    return solve_batch(1, &g, &x_dev, &b_dev, prm, info, s);
+}
+
+extern "C" cola_status cola_cg_solve_batched(int nlat, const cola_gauge *gauges, void *const *x_dev,
+                                             const void *const *b_dev, const cola_solver_params *prm,
+                                             cola_solve_info *info, cudaStream_t s) {
+    if (nlat < 1 || nlat > kMaxBatch) return arg_error("nlat must be in 1..8");
+    if (!gauges || !x_dev || !b_dev || !prm || !info) return arg_error("null argument to cola_cg_solve_batched");
+    for (int l = 0; l < nlat; ++l)
+        if (!gauges[l] || !x_dev[l] || !b_dev[l]) return arg_error("null entry in a batch array");
+    return solve_batch(nlat, gauges, x_dev, b_dev, prm, info, s);
 }
