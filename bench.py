@@ -178,8 +178,10 @@ def run_cola(args):
     u, b = make_inputs(dev)
     g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f32", "f16"), recon={"f64": 18, "f32": 12, "f16": 12})
 
+    use_graph = not args.host_loop
+
     def solve(inner="f16", bb=b, gg=g):
-        return cola.cg_solve(gg, bb, tol=TOL, op="eo", inner=inner, delta=DELTA, use_graph=True)
+        return cola.cg_solve(gg, bb, tol=TOL, op="eo", inner=inner, delta=DELTA, use_graph=use_graph)
 
     for _ in range(args.warmup):
         x, info = solve()
@@ -193,12 +195,16 @@ def run_cola(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
+    if args.profile_range:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     for _ in range(args.steps):
         x, info = solve()
         infos.append(info[0])
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -258,6 +264,8 @@ def run_cola(args):
     torch.cuda.synchronize()
     ds64_us = d0.elapsed_time(d1) * 1e3 / 20
 
+    multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
+
     # end to end through the public API with host buffers
     u_host = u.cpu().pin_memory()
     b_host = b.cpu().pin_memory()
@@ -305,6 +313,7 @@ def run_cola(args):
             "e2e": {"value": e2e_value, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": u_host.numel() * 16 + b_host.numel() * 16,
                     "d2h_bytes_per_step": x_host.numel() * 16, "ms_per_step": e2e_s * 1e3},
+            "multi_rhs": multi,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -312,6 +321,60 @@ def run_cola(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def multi_rhs_measurements(cola, dev):
+    """Multi-RHS and batched solves (not part of the timed step).
+
+    (a) the 12 spin-colour point sources at the origin on 24^3x48, kappa 0.124,
+        links exp(0.3 i H), FP32 storage with FP64 reliable updates, solved as
+        one 12-RHS graph-captured solve, against plain FP64 CG of one source;
+    (b) one batched solve of 8^4, 12^3x24, 16^3x32, 24^3x48 with 4 Gaussian
+        sources each, same parameters.
+    """
+    import torch
+
+    import synth
+
+    kappa = 0.124
+    out = {}
+    d24 = (24, 24, 24, 48)
+    u24 = synth.gauge_field(d24, 0.3, synth.seed_for(3, 0), device=dev, as_numpy=False)
+    g24 = cola.Gauge(u24, d24, kappa, BC, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
+    pts = torch.from_numpy(synth.point_sources(d24)).to(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    ms12, (x12, i12) = timed(lambda: cola.cg_solve(g24, pts, tol=TOL, op="eo", inner="f32", delta=DELTA,
+                                                   use_graph=True))
+    ms64, (x64, i64) = timed(lambda: cola.cg_solve(g24, pts[0], tol=TOL, op="eo", inner="f64", use_graph=True))
+    out["point_sources_24x24x24x48"] = {
+        "nrhs": 12, "mixed_f32_ms": ms12, "mixed_ms_per_rhs": ms12 / 12,
+        "max_iters": max(i.iters for i in i12), "max_true_rel_resid": max(i.true_rel_resid for i in i12),
+        "fp64_single_rhs_ms": ms64, "fp64_iters": i64[0].iters,
+        "per_rhs_ratio_vs_fp64": (ms12 / 12) / ms64}
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), d24]
+    gauges, bs = [], []
+    for k, d in enumerate(dims_list):
+        u = u24 if d == d24 else synth.gauge_field(d, 0.3, synth.seed_for(3, 4 + k), device=dev, as_numpy=False)
+        gauges.append(g24 if d == d24 else cola.Gauge(u, d, kappa, BC, precisions=("f64", "f32"),
+                                                      recon={"f64": 18, "f32": 12}))
+        bs.append(torch.from_numpy(synth.gaussian_spinor(d, synth.seed_for(3, 8 + k), nrhs=4)).to(dev))
+    msb, (xb, ib) = timed(lambda: cola.cg_solve_batched(gauges, bs, tol=TOL, op="eo", inner="f32", delta=DELTA,
+                                                         use_graph=True))
+    out["batched_4_lattices_x4"] = {
+        "lattices": ["8^4", "12^3x24", "16^3x32", "24^3x48"], "nrhs": 4, "ms": msb,
+        "max_iters": max(i.iters for row in ib for i in row),
+        "max_true_rel_resid": max(i.true_rel_resid for row in ib for i in row)}
+    return out
 
 
 def run_dslash_only(args):
@@ -345,6 +408,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cola", choices=["cola", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-multi-rhs", action="store_true", help="skip the multi-RHS and batched solves")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the CG loop from the host instead of one conditional CUDA graph (ncu cannot "
+                         "profile kernels inside graphs with conditional nodes)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.dslash_only:
         run_dslash_only(args)

@@ -169,7 +169,8 @@ cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity
                           cudaStream_t s) {
     if (red) {
         int pstride, ncounters, nrows = 0;
-        dslash_reduce_shape(A, nparity, default_dslash_block(prec, A.rhs_per_block), &pstride, &ncounters);
+        // sized for the smallest block the autotuner may pick (32 sites)
+        dslash_reduce_shape(A, nparity, 32, &pstride, &ncounters);
         for (int l = 0; l < A.nlat; ++l)
             if (A.lat[l].row0 + A.nrhs > nrows) nrows = A.lat[l].row0 + A.nrhs;
         COLA_TRY(ws_reduce(owner, nrows, pstride, ncounters));

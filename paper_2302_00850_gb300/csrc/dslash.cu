@@ -15,7 +15,12 @@
 // projector has rank two, so the SU(3) multiply acts on a two-spinor and
 // the other two spin rows are rebuilt from it (spin projection and
 // reconstruction, gamma matrices in the DeGrand-Rossi basis).
+#include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "cola_impl.h"
 
@@ -527,10 +532,8 @@ void dslash_reduce_shape(const DslashArgs &A, int nparity, int block_x, int *pst
     *ncounters = A.nlat * ((A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block);
 }
 
-cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
-                          int block_x, cudaStream_t s) {
-    if (block_x <= 0) block_x = default_dslash_block(prec, A.rhs_per_block);
-    if (A.nlat < 1 || A.nlat > kMaxBatch) return cudaErrorInvalidValue;
+static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+                              int block_x, cudaStream_t s) {
     const int nb = assign_blocks(A, block_x);
     A.ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
     switch (prec) {
@@ -544,6 +547,140 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
             return recon == 12 ? launch_r<COLA_F16, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
                                : launch_r<COLA_F16, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
     }
+}
+
+// ---------------------------------------------------------------- autotune --
+// Launch shape (threads per block along sites, right-hand sides per block)
+// chosen per configuration by timing the candidates on the caller's stream
+// the first time a configuration is seen outside stream capture.  The
+// timed launches write only `out` (never an input), without the fused
+// reduction or solver-state filtering, so tuning changes no result.  Entries
+// are kept per process and, with COLA_TUNE_CACHE=<file>, in that file.
+// COLA_TUNE=0 disables tuning (defaults are used).
+struct TuneEntry {
+    int bx, by;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneEntry> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_key(int prec, int recon, const DslashArgs &A, int nparity, bool dagger, bool xpay) {
+    std::string k = "dslash p" + std::to_string(prec) + " r" + std::to_string(recon) + " d" + std::to_string(dagger) +
+                    " x" + std::to_string(xpay) + " np" + std::to_string(nparity) + " n" + std::to_string(A.nrhs) +
+                    " s" + std::to_string(staged_depth(prec));
+    for (int l = 0; l < A.nlat; ++l) {
+        const Geom &g = A.lat[l].g;
+        k += " " + std::to_string(g.L[0]) + "x" + std::to_string(g.L[1]) + "x" + std::to_string(g.L[2]) + "x" +
+             std::to_string(g.L[3]);
+    }
+    return k;
+}
+
+static void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("COLA_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+        char *bar = strrchr(line, '|');
+        if (!bar) continue;
+        int bx = 0, by = 0;
+        if (sscanf(bar + 1, "%d %d", &bx, &by) != 2 || bx < 32 || by < 1) continue;
+        *bar = 0;
+        g_tune[std::string(line)] = {bx, by};
+    }
+    fclose(f);
+}
+
+static void tune_store_locked(const std::string &key, TuneEntry e) {
+    g_tune[key] = e;
+    const char *path = getenv("COLA_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s|%d %d\n", key.c_str(), e.bx, e.by);
+    fclose(f);
+}
+
+static bool tuning_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("COLA_TUNE");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+static bool outputs_alias_inputs(const DslashArgs &A) {
+    for (int l = 0; l < A.nlat; ++l)
+        if (A.lat[l].out == A.lat[l].in || A.lat[l].out == A.lat[l].xin) return true;
+    return false;
+}
+
+static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bool dagger, bool xpay,
+                      cudaStream_t s) {
+    TuneEntry best = {default_dslash_block(prec, A0.rhs_per_block), A0.rhs_per_block};
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return best;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return best;
+    }
+    const int bys[] = {1, 2, 4, 8};
+    const int bxs[] = {32, 64, 128, 256};
+    for (int by : bys) {
+        if (by > A0.nrhs) continue;
+        for (int bx : bxs) {
+            if (bx * by > 256 || bx * by < 64) continue;
+            DslashArgs A = A0;
+            A.rhs_per_block = by;
+            A.state = nullptr;
+            A.filter_ru = 0;
+            bool ok = launch_now(prec, recon, A, nparity, dagger, xpay, false, bx, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_now(prec, recon, A, nparity, dagger, xpay, false, bx, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.f;
+            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best = {bx, by};
+            }
+            cudaGetLastError();
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+                          int block_x, cudaStream_t s) {
+    if (A.nlat < 1 || A.nlat > kMaxBatch) return cudaErrorInvalidValue;
+    if (block_x <= 0) {
+        block_x = default_dslash_block(prec, A.rhs_per_block);
+        if (tuning_enabled()) {
+            const std::string key = tune_key(prec, recon, A, nparity, dagger, xpay);
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            tune_load_locked();
+            auto it = g_tune.find(key);
+            if (it == g_tune.end()) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+                    !outputs_alias_inputs(A)) {
+                    tune_store_locked(key, tune(prec, recon, A, nparity, dagger, xpay, s));
+                    it = g_tune.find(key);
+                }
+            }
+            if (it != g_tune.end()) {
+                block_x = it->second.bx;
+                A.rhs_per_block = it->second.by;
+            }
+        }
+    }
+    return launch_now(prec, recon, A, nparity, dagger, xpay, red, block_x, s);
 }
 
 // Threads per block along the sites; COLA_DSLASH_BLOCK overrides (tuning runs).

@@ -406,6 +406,12 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
                 COLA_CUDA(cudaMemsetAsync(static_cast<char *>(c.lat[l].xhi) + r * hi1, 0, hi1, s), "zero x");
         }
     }
+    if (running && prm->use_graph) {
+        // Kernels launched while a stream is capturing are not autotuned, so
+        // tune the inner operator once here: q = A p is recomputed by the
+        // first iteration before anything reads it.
+        COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, nullptr, false, false, s));
+    }
     if (running) COLA_TRY(prm->use_graph ? run_graph_loop(c, s) : run_host_loop(c, s));
     {
         // a row stopped by breakdown may still hold work in x_lo
