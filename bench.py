@@ -397,8 +397,31 @@ def run_dslash_only(args):
     print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps}))
 
 
+def run_solve_only(args):
+    """One mixed-precision even-odd solve on a smaller lattice (the case profiled with ncu)."""
+    import torch
+
+    import paper_2302_00850_gb300 as cola
+    import synth
+
+    torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.lattice.split("x"))
+    dev = torch.device("cuda", 0)
+    u = synth.gauge_field(dims, EPS, synth.seed_for(CONFIG_ID, 0), device=dev, as_numpy=False)
+    b = torch.from_numpy(synth.gaussian_spinor(dims, synth.seed_for(CONFIG_ID, 1))).to(dev)
+    g = cola.Gauge(u, dims, KAPPA, BC, precisions=("f64", args.prec), recon={"f64": 18, args.prec: 12})
+    del u
+    for _ in range(args.reps):
+        x, info = cola.cg_solve(g, b, tol=TOL, op="eo", inner=args.prec, delta=DELTA, use_graph=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_only": args.lattice, "prec": args.prec, "iters": info[0].iters,
+                      "true_rel_resid": info[0].true_rel_resid}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--solve-only", action="store_true", help="run host-loop solves on --lattice and exit")
+    ap.add_argument("--lattice", default="24x24x24x48")
     ap.add_argument("--dslash-only", action="store_true", help="run chained parity Dslash applies and exit")
     ap.add_argument("--prec", default="f16")
     ap.add_argument("--recon", type=int, default=12)
@@ -417,6 +440,8 @@ def main():
     args = ap.parse_args()
     if args.dslash_only:
         run_dslash_only(args)
+    elif args.solve_only:
+        run_solve_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

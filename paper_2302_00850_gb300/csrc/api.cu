@@ -165,24 +165,13 @@ DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, c
     return A;
 }
 
-cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
+cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
                           cudaStream_t s) {
-    if (red) {
-        int pstride, ncounters, nrows = 0;
-        // sized for the smallest block the autotuner may pick (32 sites)
-        dslash_reduce_shape(A, nparity, 32, &pstride, &ncounters);
-        for (int l = 0; l < A.nlat; ++l)
-            if (A.lat[l].row0 + A.nrhs > nrows) nrows = A.lat[l].row0 + A.nrhs;
-        COLA_TRY(ws_reduce(owner, nrows, pstride, ncounters));
-        A.partials = owner->partials;
-        A.pstride = pstride;
-        A.counters = owner->counters;
-    }
-    return cuda_check(launch_dslash(prec, owner->recon[prec], A, nparity, dagger, xpay, red, 0, s), "dslash launch");
+    return cuda_check(launch_dslash(prec, owner->recon[prec], A, nparity, dagger, xpay, 0, s), "dslash launch");
 }
 
 cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
-                              bool reduce, cudaStream_t s) {
+                              cudaStream_t s) {
     cola_gauge owner = L[0].g;
     auto batch = [&](int parity0, double a_coef, bool use_xin, int which) {
         // which: 0 in->t, 1 t->mp (xin = in), 2 mp->t, 3 t->out (xin = mp); full: 4 in->mp, 5 mp->out
@@ -203,24 +192,24 @@ cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nr
     };
     if (op == COLA_OP_EO) {
         DslashArgs A = batch(1, 0.0, false, 0);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, false, false, false, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, false, s));
         A = batch(0, 1.0, true, 1);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, false, true, reduce, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, true, s));
         A = batch(1, 0.0, false, 2);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, true, false, false, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, true, false, s));
         A = batch(0, 1.0, true, 3);
-        return dslash_launch(owner, prec, A, 1, true, true, false, s);
+        return dslash_launch(owner, prec, A, 1, true, true, s);
     }
     DslashArgs A = batch(0, 1.0, true, 4);
-    COLA_TRY(dslash_launch(owner, prec, A, 2, false, true, reduce, s));
+    COLA_TRY(dslash_launch(owner, prec, A, 2, false, true, s));
     A = batch(0, 1.0, true, 5);
-    return dslash_launch(owner, prec, A, 2, true, true, false, s);
+    return dslash_launch(owner, prec, A, 2, true, true, s);
 }
 
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
-                        CgState *st, bool filter_ru, bool reduce, cudaStream_t s) {
+                        CgState *st, bool filter_ru, cudaStream_t s) {
     OpLat L = {g, out, in, t, mp, 0};
-    return apply_mdagm_batch(1, &L, prec, op, nrhs, st, filter_ru, reduce, s);
+    return apply_mdagm_batch(1, &L, prec, op, nrhs, st, filter_ru, s);
 }
 
 }  // namespace cola
@@ -314,7 +303,7 @@ cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const voi
     COLA_TRY(check_rhs(nrhs));
     const bool xpay = a != 0.0;
     DslashArgs A = make_dslash_args(g, prec, out, in, xpay ? in_self : nullptr, nrhs, parity == 2 ? 0 : parity, a, b);
-    return dslash_launch(g, prec, A, parity == 2 ? 2 : 1, dagger != 0, xpay, false, stream);
+    return dslash_launch(g, prec, A, parity == 2 ? 2 : 1, dagger != 0, xpay, stream);
 }
 
 cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec, int nrhs,
@@ -328,7 +317,7 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
     void *t, *mp;
     COLA_TRY(ws_slot(g, 0, bytes, &t));
     COLA_TRY(ws_slot(g, 1, bytes, &mp));
-    return apply_mdagm(g, prec, op, out, in, t, mp, nrhs, nullptr, false, false, stream);
+    return apply_mdagm(g, prec, op, out, in, t, mp, nrhs, nullptr, false, stream);
 }
 
 cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_dev, const void *Y_dev,

@@ -59,7 +59,12 @@ __device__ __forceinline__ double site_norm2(const Cx<R> (&s)[12]) {
     return (double)a;
 }
 
-__device__ __forceinline__ int row_nblocks(const BlasArgs &B, const SiteRef &r) { return B.lat[r.l].nblocks; }
+// Warp-granular grid reduction of one row (every warp of the launch takes part).
+__device__ __forceinline__ bool blas_reduce(const BlasArgs &B, const SiteRef &r, double v, double *tot) {
+    const int wpb = blockDim.x >> 5;
+    return reduce_warp_rows(v, B.partials, B.pstride, r.row, B.counters + (size_t)r.row * B.cstride,
+                            B.lat[r.l].nblocks * wpb, r.bid * wpb + (threadIdx.x >> 5), tot);
+}
 
 // ---------------------------------------------------------------------------
 // slots (x, r, p, q):  x += alpha p;  r -= alpha q;  rho_new = |r|^2
@@ -67,7 +72,6 @@ template <int PX, int PV>
 __global__ void __launch_bounds__(256) cg_update_xr_kernel(const __grid_constant__ BlasArgs B) {
     using RV = typename Prec<PV>::real;
     using RX = typename Prec<PX>::real;
-    __shared__ double sh[32];
     const SiteRef r = blas_site(B);
     CgState &S = B.state[r.row];
     const bool live = !S.done;
@@ -95,9 +99,8 @@ __global__ void __launch_bounds__(256) cg_update_xr_kernel(const __grid_constant
         nr = site_norm2(rv);
     }
     double tot;
-    if (reduce_rows_last_block(nr, B.partials, B.pstride, r.row, B.counters + r.row, row_nblocks(B, r), r.bid, true,
-                               sh, &tot)) {
-        if (threadIdx.x == 0 && live) {
+    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
+        {
             S.rho_new = tot;
             S.iter += 1;
             if (!isfinite(tot)) {
@@ -130,6 +133,30 @@ __global__ void __launch_bounds__(256) cg_update_p_kernel(const __grid_constant_
     SpinorIO<PV>::store(vptr_w(B, r, 0), vh, r.cb, pv);
 }
 
+// slot (mp):  pq = |M p|^2 = <p, A p>;  rho = rho_new;  alpha = rho / pq
+template <int PV>
+__global__ void __launch_bounds__(256) cg_pq_kernel(const __grid_constant__ BlasArgs B) {
+    const SiteRef r = blas_site(B);
+    CgState &S = B.state[r.row];
+    const bool live = !S.done;
+    double nr = 0.0;
+    if (live && r.ok) {
+        Cx<typename Prec<PV>::real> m[12];
+        SpinorIO<PV>::load(vptr(B, r, 0), B.lat[r.l].vh, r.cb, m);
+        nr = site_norm2(m);
+    }
+    double tot;
+    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
+        S.pq = tot;
+        S.rho = S.rho_new;
+        S.alpha = S.rho / tot;
+        if (!(tot > 0.0) || !isfinite(S.alpha)) {
+            S.status = COLA_ERR_BREAKDOWN;
+            S.done = 1;
+        }
+    }
+}
+
 // slots (x_hi, x_lo):  x_hi += x_lo;  x_lo = 0
 template <int PX>
 __global__ void __launch_bounds__(256) ru_accumulate_kernel(const __grid_constant__ BlasArgs B, int force) {
@@ -156,7 +183,6 @@ __global__ void __launch_bounds__(256) ru_accumulate_kernel(const __grid_constan
 // |r_hi|^2 -> r2_last, rho_new; converged / cap / breakdown decisions.
 template <int PV>
 __global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant__ BlasArgs B) {
-    __shared__ double sh[32];
     const SiteRef r = blas_site(B);
     CgState &S = B.state[r.row];
     const bool live = B.init ? true : (S.ru && !S.done);
@@ -179,9 +205,8 @@ __global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant_
         nr = site_norm2(bv);
     }
     double tot;
-    if (reduce_rows_last_block(nr, B.partials, B.pstride, r.row, B.counters + r.row, row_nblocks(B, r), r.bid, true,
-                               sh, &tot)) {
-        if (threadIdx.x == 0 && live) {
+    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
+        {
             S.rho_new = tot;
             S.r2_last = tot;
             S.ru = 0;
@@ -203,7 +228,6 @@ __global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant_
 // slot (v):  |v|^2 per row; with init_norms, b2 and tol2 of the state.
 template <int P>
 __global__ void __launch_bounds__(256) norm2_kernel(const __grid_constant__ BlasArgs B, int init_norms) {
-    __shared__ double sh[32];
     const SiteRef r = blas_site(B);
     double nr = 0.0;
     if (r.ok) {
@@ -212,9 +236,8 @@ __global__ void __launch_bounds__(256) norm2_kernel(const __grid_constant__ Blas
         nr = site_norm2(a);
     }
     double tot;
-    if (reduce_rows_last_block(nr, B.partials, B.pstride, r.row, B.counters + r.row, row_nblocks(B, r), r.bid, true,
-                               sh, &tot)) {
-        if (threadIdx.x == 0) {
+    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0) {
+        {
             if (B.out) B.out[r.row] = tot;
             if (init_norms) {
                 CgState &S = B.state[r.row];
@@ -273,13 +296,13 @@ static dim3 blas_grid(BlasArgs &B) {
     return dim3(total, B.nrhs);
 }
 
-int blas_pstride(const BlasArgs &B) {
+int blas_max_warps(const BlasArgs &B) {
     int mx = 0;
     for (int l = 0; l < B.nlat; ++l) {
         const int nb = (B.lat[l].vh * B.nparity + kBlasBlock - 1) / kBlasBlock;
         if (nb > mx) mx = nb;
     }
-    return mx;
+    return mx * (kBlasBlock / 32);
 }
 
 cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s) {
@@ -295,6 +318,14 @@ cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s) {
     if (B.prec[0] == COLA_F64) cg_update_p_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
     else if (B.prec[0] == COLA_F32) cg_update_p_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
     else cg_update_p_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s) {
+    const dim3 g = blas_grid(B);
+    if (B.prec[0] == COLA_F64) cg_pq_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
+    else if (B.prec[0] == COLA_F32) cg_pq_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
+    else cg_pq_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
     return cudaGetLastError();
 }
 

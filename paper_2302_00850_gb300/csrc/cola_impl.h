@@ -35,22 +35,16 @@ struct DslashArgs {
     int rhs_per_block;
     int parity0;                  // first output parity (blockIdx.z adds 0 or 1)
     DslashLat lat[kMaxBatch];
-    // fused |out|^2 reduction (when launched with red = true)
-    double *partials;             // [row][pstride]
-    int pstride;
-    unsigned *counters;           // [lattice][rhs group], zero between launches
-    int ngroups;
-    double *result;               // [row] sums (when state == nullptr)
-    CgState *state;               // solver mode: skips finished rows; with red, sets pq and alpha
+    CgState *state;               // solver mode: skip finished rows
     int filter_ru;                // with state: compute only rows with a pending reliable update
+    int ngroups;                  // right-hand-side groups (set by launch_dslash)
 };
 
 int default_dslash_block(int prec, int rhs_per_block);
-// Fills block0/nblocks of every lattice for block_x and launches.
-cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
-                          int block_x, cudaStream_t s);
-// Largest per-row partials count and counters a launch of A needs.
-void dslash_reduce_shape(const DslashArgs &A, int nparity, int block_x, int *pstride, int *ncounters);
+// Fills block0/nblocks of every lattice and launches; block_x <= 0 picks the
+// autotuned (or default) launch shape.
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
+                          cudaStream_t s);
 
 // ---------------------------------------------------------------- packing --
 cudaError_t launch_pack_gauge(int prec, int recon, const Geom &g, void *packed, const void *canon,
@@ -84,24 +78,26 @@ struct BlasArgs {
     CgState *state;
     double *partials;
     int pstride;
-    unsigned *counters;   // one per row
+    unsigned *counters;   // [row][cstride]
+    int cstride;
     double *out;          // norm2 results per row
     double a, b;          // axpby coefficients
     int init;             // ru_residual: initial residual (every row, also writes p)
 };
 
-// Slots: update_xr (x, r, p, q); update_p (p, r); ru_accumulate (x_hi, x_lo);
+// Slots: update_xr (x, r, p, q); update_p (p, r); pq (mp); ru_accumulate (x_hi, x_lo);
 // ru_residual (r_hi, b, ax, r_lo, p); norm2 (v); convert (dst, src); axpby (dst, x, y).
 cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s);         // slot (mp): pq, rho, alpha
 cudaError_t launch_ru_accumulate(BlasArgs &B, bool force, cudaStream_t s);
 cudaError_t launch_ru_residual(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_init_norms(BlasArgs &B, cudaStream_t s);   // st.b2 = |b|^2, st.tol2 *= |b|^2
 cudaError_t launch_norm2(BlasArgs &B, cudaStream_t s);        // out[row] = |v|^2
 cudaError_t launch_convert(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_axpby(BlasArgs &B, cudaStream_t s);
-// Per-row partials count the batched vector kernels need.
-int blas_pstride(const BlasArgs &B);
+// Largest warp count per row of the batched vector kernels.
+int blas_max_warps(const BlasArgs &B);
 
 // ----------------------------------------------------------------- force --
 cudaError_t launch_force(const Geom &g, double kappa, const void *links_f64, int recon, double *force,
@@ -159,16 +155,16 @@ DslashLat make_dslash_lat(cola_gauge g, int prec, void *out, const void *in, con
                           int row0);
 DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
                             int parity0, double a, double b);
-// Launch a (batched) hopping term; reduction scratch comes from `owner`.
+// Launch a (batched) hopping term with the links of `owner`'s reconstruction.
 cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
-                          bool red, cudaStream_t s);
-// out = Mdag M in for every lattice of L (op EO: Mhat on even halves; op
-// FULL: D).  With st != nullptr rows are filtered by st (filter_ru: only rows
-// with a pending reliable update) and, with reduce, the first xpay apply
-// reduces |M in|^2 into st (pq, alpha).  Scratch comes from L[0].g.
+                          cudaStream_t s);
+// out = Mdag M in for every lattice of L (op EO: Mhat on even halves, with
+// Mhat in left in mp; op FULL: D, with D in left in mp).  With st != nullptr
+// rows are filtered by st (filter_ru: only rows with a pending reliable
+// update).
 cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
-                              bool reduce, cudaStream_t s);
+                              cudaStream_t s);
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
-                        CgState *st, bool filter_ru, bool reduce, cudaStream_t s);
+                        CgState *st, bool filter_ru, cudaStream_t s);
 cola_status cuda_check(cudaError_t e, const char *what);
 }  // namespace cola

@@ -372,52 +372,78 @@ struct CgState {
     int status;
 };
 
-// Sum over the threads of each row threadIdx.y of the block, fixed order.
-// blockDim.x must be a multiple of 32.  The sum is valid in threadIdx.x == 0.
-__device__ __forceinline__ double row_sum(double v, double *sh) {
-    const int lane = threadIdx.x & 31;
-    const int wrow = threadIdx.x >> 5;
-    const int wpr = blockDim.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[threadIdx.y * wpr + wrow] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < wpr; ++w) r += sh[threadIdx.y * wpr + w];
-    }
-    return r;
+// Deterministic two-level grid reduction at warp granularity (no
+// floating-point atomics, no block barriers).  Every warp of a row writes
+// its sum to part[row][warp_id]; warps are grouped kRedGroup at a time and
+// the last warp of a group to arrive (atomic ticket on the group's counter)
+// sums the group's partials in warp order into part[row][nwarps + group]; the
+// last group to finish sums those in group order.  Loads use ld.global.cg
+// (the partials come from other SMs, so L1 is bypassed).  Because no warp
+// waits for the other warps of its block, a reducing kernel runs as fast as
+// its non-reducing twin apart from the final few L2 round trips.
+// Scratch per row: part needs red_pstride(nwarps) doubles, counters
+// red_cstride(nwarps) (cnt[0] final, cnt[1 + g] group g).  Counters are reset
+// by their last user, so they are zero between launches.
+// Returns true in the lanes of the warp that finished the row; *out then
+// holds the row's sum (all lanes).
+constexpr int kRedGroup = 32;
+
+__host__ __device__ constexpr int red_groups(int nwarps) { return (nwarps + kRedGroup - 1) / kRedGroup; }
+__host__ __device__ constexpr int red_pstride(int nwarps) { return nwarps + red_groups(nwarps); }
+__host__ __device__ constexpr int red_cstride(int nwarps) { return 1 + red_groups(nwarps); }
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Two-stage deterministic reduction: every block writes its row sums to
-// partials[row * pstride + block_id]; the last block of the row group to
-// arrive (atomic ticket) sums each row's partials in block order.  Returns
-// true in the threads of the last block; `*out_row_sum` then holds the sum of
-// the calling thread's row (valid in threadIdx.x == 0).  `counter` is reset by
-// the last block, so the next launch starts from zero.
-__device__ __forceinline__ bool reduce_rows_last_block(double v, double *partials, int pstride, int row_global,
-                                                       unsigned *counter, int nblocks, int block_id,
-                                                       bool row_valid, double *sh, double *out_row_sum) {
-    __shared__ bool am_last;
-    double s = row_sum(v, sh);
-    if (threadIdx.x == 0 && row_valid) partials[(size_t)row_global * pstride + block_id] = s;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        unsigned ticket = atomicAdd(counter, 1u);
-        am_last = (ticket == (unsigned)nblocks - 1);
-    }
-    __syncthreads();
-    if (!am_last) return false;
-    __threadfence();
+// Sum of p[0..n) in a fixed order across one warp (eight loads in flight per lane).
+__device__ __forceinline__ double warp_sum_of(const double *p, int n) {
+    const int lane = threadIdx.x & 31;
     double acc = 0.0;
-    if (row_valid) {
-        const volatile double *pr = partials + (size_t)row_global * pstride;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += pr[b];
+    for (int base = 0; base < n; base += 256) {
+        double a[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int b = base + lane + 32 * k;
+            a[k] = b < n ? __ldcg(p + b) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += a[k];
     }
-    double tot = row_sum(acc, sh);
-    if (threadIdx.x == 0) *out_row_sum = tot;
-    if (threadIdx.x == 0 && threadIdx.y == 0) *counter = 0u;
+    return warp_allsum(acc);
+}
+
+__device__ __forceinline__ bool reduce_warp_rows(double v, double *partials, int pstride, int row, unsigned *cnt,
+                                                 int nwarps, int warp_id, double *out) {
+    const int lane = threadIdx.x & 31;
+    double *part = partials + (size_t)row * pstride;
+    const double s = warp_allsum(v);
+    const int grp = warp_id / kRedGroup;
+    const int gsize = min(kRedGroup, nwarps - grp * kRedGroup);
+    const int ngrp = red_groups(nwarps);
+    unsigned ticket = 0;
+    if (lane == 0) {
+        part[warp_id] = s;
+        __threadfence();
+        ticket = atomicAdd(cnt + 1 + grp, 1u);
+        __threadfence();
+    }
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket != (unsigned)gsize - 1) return false;
+    const double gs = warp_sum_of(part + grp * kRedGroup, gsize);
+    if (lane == 0) {
+        part[nwarps + grp] = gs;
+        cnt[1 + grp] = 0u;
+        __threadfence();
+        ticket = atomicAdd(cnt, 1u);
+        __threadfence();
+    }
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket != (unsigned)ngrp - 1) return false;
+    *out = warp_sum_of(part + nwarps, ngrp);
+    if (lane == 0) cnt[0] = 0u;
     return true;
 }
 

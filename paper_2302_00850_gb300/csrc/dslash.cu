@@ -15,6 +15,7 @@
 // projector has rank two, so the SU(3) multiply acts on a two-spinor and
 // the other two spin rows are rebuilt from it (spin projection and
 // reconstruction, gamma matrices in the DeGrand-Rossi basis).
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -365,10 +366,16 @@ __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, 
 // Grid: x over the site blocks of every lattice of the batch (lattice l owns
 // blocks [block0, block0 + nblocks)), y over right-hand-side groups, z over
 // the output parities (1 or 2).  Block: (sites, right-hand sides).
-template <int P, int RECON, bool DAGGER, bool XPAY, bool RED, int NS>
-__global__ void __launch_bounds__(256, COLA_DSLASH_MINB) dslash_kernel(const __grid_constant__ DslashArgs A) {
+// Register budget: FP16/FP32 at two 256-thread blocks per SM (128 registers,
+// no spills); FP64 is bound by the FP64 pipe and keeps its full register set.
+template <int P>
+struct MinBlocks {
+    static constexpr int value = P == COLA_F64 ? 1 : COLA_DSLASH_MINB;
+};
+
+template <int P, int RECON, bool DAGGER, bool XPAY, int NS>
+__global__ void __launch_bounds__(256, MinBlocks<P>::value) dslash_kernel(const __grid_constant__ DslashArgs A) {
     using R = typename Prec<P>::real;
-    __shared__ double sh[32];
     int l = 0;
     while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
     const DslashLat &L = A.lat[l];
@@ -383,13 +390,13 @@ __global__ void __launch_bounds__(256, COLA_DSLASH_MINB) dslash_kernel(const __g
         const CgState &st = A.state[row];
         live = A.filter_ru ? (st.ru && !st.done) : !st.done;
     }
-    double nrm = 0.0;
-    if (cb < g.Vh && live) {
+    const bool have = cb < g.Vh && live;
+    Cx<R> acc[12];
+    if (have) {
         const Coord c = cb_coord(g, cb, par);
         const char *in = static_cast<const char *>(L.in) + rhs * L.rhs_stride + (1 - par) * L.parity_stride;
         const char *lo = static_cast<const char *>(L.links) + par * L.link_parity_stride;
         const char *li = static_cast<const char *>(L.links) + (1 - par) * L.link_parity_stride;
-        Cx<R> acc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
         if constexpr (NS > 0 && P != COLA_F64) {
@@ -418,39 +425,9 @@ __global__ void __launch_bounds__(256, COLA_DSLASH_MINB) dslash_kernel(const __g
                 acc[k].im *= b;
             }
         }
-        SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb,
-                           acc);
-        if constexpr (RED) {
-            R s2 = R(0);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) s2 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
-            nrm = (double)s2;
-        }
     }
-    if constexpr (RED) {
-        const int nblocks = L.nblocks * gridDim.z;
-        const int bid = blockIdx.z * L.nblocks + ((int)blockIdx.x - L.block0);
-        double tot;
-        if (reduce_rows_last_block(nrm, A.partials, A.pstride, row, A.counters + l * A.ngroups + blockIdx.y,
-                                   nblocks, bid, row_ok, sh, &tot)) {
-            if (threadIdx.x == 0 && row_ok) {
-                if (A.state) {
-                    CgState &st = A.state[row];
-                    if (!st.done) {
-                        st.pq = tot;
-                        st.rho = st.rho_new;
-                        st.alpha = st.rho / tot;
-                        if (!(tot > 0.0) || !isfinite(st.alpha)) {
-                            st.status = COLA_ERR_BREAKDOWN;
-                            st.done = 1;
-                        }
-                    }
-                } else if (A.result) {
-                    A.result[row] = tot;
-                }
-            }
-        }
-    }
+    if (have)
+        SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb, acc);
 }
 
 // Pipeline depth of the staged kernels: FP16 storage moves half the bytes
@@ -466,7 +443,7 @@ static int staged_depth(int prec) {
     return prec == COLA_F16 ? 3 : 0;
 }
 
-template <int P, int RECON, bool DAGGER, bool XPAY, bool RED, int NS>
+template <int P, int RECON, bool DAGGER, bool XPAY, int NS>
 static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total_blocks, cudaStream_t s) {
     const int by = A.rhs_per_block;
     dim3 block(bx, by, 1);
@@ -476,38 +453,32 @@ static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total
         smem = (size_t)NS * HopLayout<P, RECON>::bytes * bx * by;
         static bool attr_set = false;
         if (!attr_set) {
-            cudaFuncSetAttribute(dslash_kernel<P, RECON, DAGGER, XPAY, RED, NS>,
+            cudaFuncSetAttribute(dslash_kernel<P, RECON, DAGGER, XPAY, NS>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
             attr_set = true;
         }
     }
-    dslash_kernel<P, RECON, DAGGER, XPAY, RED, NS><<<grid, block, smem, s>>>(A);
+    dslash_kernel<P, RECON, DAGGER, XPAY, NS><<<grid, block, smem, s>>>(A);
     return cudaGetLastError();
 }
 
-template <int P, int RECON, bool DAGGER, bool XPAY, bool RED>
+template <int P, int RECON, bool DAGGER, bool XPAY>
 static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cudaStream_t s) {
     if constexpr (P == COLA_F64) {
-        return launch_ns<P, RECON, DAGGER, XPAY, RED, 0>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, XPAY, 0>(A, nparity, bx, nb, s);
     } else {
-        if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, XPAY, RED, 0>(A, nparity, bx, nb, s);
-        return launch_ns<P, RECON, DAGGER, XPAY, RED, 3>(A, nparity, bx, nb, s);
+        if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, XPAY, 0>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, XPAY, 3>(A, nparity, bx, nb, s);
     }
 }
 
 template <int P, int RECON>
-static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, bool xpay, bool red, int bx, int nb,
+static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, bool xpay, int bx, int nb,
                             cudaStream_t s) {
-    if (dagger) {
-        if (xpay) return red ? launch_t<P, RECON, true, true, true>(A, nparity, bx, nb, s)
-                             : launch_t<P, RECON, true, true, false>(A, nparity, bx, nb, s);
-        return red ? launch_t<P, RECON, true, false, true>(A, nparity, bx, nb, s)
-                   : launch_t<P, RECON, true, false, false>(A, nparity, bx, nb, s);
-    }
-    if (xpay) return red ? launch_t<P, RECON, false, true, true>(A, nparity, bx, nb, s)
-                         : launch_t<P, RECON, false, true, false>(A, nparity, bx, nb, s);
-    return red ? launch_t<P, RECON, false, false, true>(A, nparity, bx, nb, s)
-               : launch_t<P, RECON, false, false, false>(A, nparity, bx, nb, s);
+    if (dagger) return xpay ? launch_t<P, RECON, true, true>(A, nparity, bx, nb, s)
+                            : launch_t<P, RECON, true, false>(A, nparity, bx, nb, s);
+    return xpay ? launch_t<P, RECON, false, true>(A, nparity, bx, nb, s)
+                : launch_t<P, RECON, false, false>(A, nparity, bx, nb, s);
 }
 
 // Site blocks per lattice for block_x; returns the total.
@@ -521,31 +492,20 @@ static int assign_blocks(DslashArgs &A, int bx) {
     return total;
 }
 
-void dslash_reduce_shape(const DslashArgs &A, int nparity, int block_x, int *pstride, int *ncounters) {
-    const int bx = block_x > 0 ? block_x : default_dslash_block(0, A.rhs_per_block);
-    int mx = 0;
-    for (int l = 0; l < A.nlat; ++l) {
-        const int nb = (A.lat[l].g.Vh + bx - 1) / bx;
-        if (nb > mx) mx = nb;
-    }
-    *pstride = mx * nparity;
-    *ncounters = A.nlat * ((A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block);
-}
-
-static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
-                              int block_x, cudaStream_t s) {
+static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
+                              cudaStream_t s) {
     const int nb = assign_blocks(A, block_x);
     A.ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
     switch (prec) {
         case COLA_F64:
-            return recon == 12 ? launch_r<COLA_F64, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
-                               : launch_r<COLA_F64, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
+            return recon == 12 ? launch_r<COLA_F64, 12>(A, nparity, dagger, xpay, block_x, nb, s)
+                               : launch_r<COLA_F64, 18>(A, nparity, dagger, xpay, block_x, nb, s);
         case COLA_F32:
-            return recon == 12 ? launch_r<COLA_F32, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
-                               : launch_r<COLA_F32, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
+            return recon == 12 ? launch_r<COLA_F32, 12>(A, nparity, dagger, xpay, block_x, nb, s)
+                               : launch_r<COLA_F32, 18>(A, nparity, dagger, xpay, block_x, nb, s);
         default:
-            return recon == 12 ? launch_r<COLA_F16, 12>(A, nparity, dagger, xpay, red, block_x, nb, s)
-                               : launch_r<COLA_F16, 18>(A, nparity, dagger, xpay, red, block_x, nb, s);
+            return recon == 12 ? launch_r<COLA_F16, 12>(A, nparity, dagger, xpay, block_x, nb, s)
+                               : launch_r<COLA_F16, 18>(A, nparity, dagger, xpay, block_x, nb, s);
     }
 }
 
@@ -639,9 +599,9 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
             A.rhs_per_block = by;
             A.state = nullptr;
             A.filter_ru = 0;
-            bool ok = launch_now(prec, recon, A, nparity, dagger, xpay, false, bx, s) == cudaSuccess;
+            bool ok = launch_now(prec, recon, A, nparity, dagger, xpay, bx, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-            for (int r = 0; r < 3 && ok; ++r) ok = launch_now(prec, recon, A, nparity, dagger, xpay, false, bx, s) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_now(prec, recon, A, nparity, dagger, xpay, bx, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0.f;
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
@@ -656,8 +616,8 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
     return best;
 }
 
-cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, bool red,
-                          int block_x, cudaStream_t s) {
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
+                          cudaStream_t s) {
     if (A.nlat < 1 || A.nlat > kMaxBatch) return cudaErrorInvalidValue;
     if (block_x <= 0) {
         block_x = default_dslash_block(prec, A.rhs_per_block);
@@ -680,7 +640,7 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
             }
         }
     }
-    return launch_now(prec, recon, A, nparity, dagger, xpay, red, block_x, s);
+    return launch_now(prec, recon, A, nparity, dagger, xpay, block_x, s);
 }
 
 // Threads per block along the sites; COLA_DSLASH_BLOCK overrides (tuning runs).

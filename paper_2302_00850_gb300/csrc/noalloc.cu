@@ -89,5 +89,5 @@ extern "C" cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const v
     cola_status st = static_scratch(&w);
     if (st != COLA_OK) return st;
     // t (odd half) and mp (even half) share the one scratch field
-    return cola::apply_mdagm(g, prec, op, out, in, w, w, nrhs, nullptr, false, false, stream);
+    return cola::apply_mdagm(g, prec, op, out, in, w, w, nrhs, nullptr, false, stream);
 }

@@ -13,10 +13,10 @@
 // residual.  With inner = FP64 the same loop is the plain FP64 CG, whose
 // "reliable update" is the true-residual confirmation at convergence.
 //
-// Per iteration: four hopping-term launches for A = Mhat^dag Mhat (the
-// second also reduces <p, Ap> = |Mhat p|^2 and sets alpha), one fused
-// x/r update that reduces |r|^2 and decides, optionally the FP64 update,
-// and the p update.  All scalars stay on the device.  Two drivers run the
+// Per iteration: four hopping-term launches for A = Mhat^dag Mhat, one
+// reduction of <p, Ap> = |Mhat p|^2 that sets alpha, one fused x/r update
+// that reduces |r|^2 and decides, optionally the FP64 update, and the p
+// update.  All scalars stay on the device.  Two drivers run the
 // loop: a host loop that reads the per-right-hand-side state after each
 // update, or one CUDA graph whose while/if conditional nodes are set by a
 // one-thread control kernel, so that a whole solve is a single launch.
@@ -113,30 +113,33 @@ BlasArgs blas(const SolveCtx &c, std::initializer_list<std::pair<VecId, int>> id
     }
     B.state = c.owner->states;
     B.partials = c.owner->partials;
-    B.pstride = blas_pstride(B);
+    B.pstride = red_pstride(blas_max_warps(B));
     B.counters = c.owner->counters;
+    B.cstride = red_cstride(blas_max_warps(B));
     return B;
 }
 
 cola_status mdagm(const SolveCtx &c, int prec, VecId out, VecId in, VecId t, VecId mp, CgState *st, bool filter_ru,
-                  bool reduce, cudaStream_t s) {
+                  cudaStream_t s) {
     OpLat L[kMaxBatch];
     for (int l = 0; l < c.nlat; ++l)
         L[l] = {c.lat[l].g, vec(c.lat[l], out), vec(c.lat[l], in), vec(c.lat[l], t), vec(c.lat[l], mp), c.lat[l].row0};
-    return apply_mdagm_batch(c.nlat, L, prec, c.op, c.nrhs, st, filter_ru, reduce, s);
+    return apply_mdagm_batch(c.nlat, L, prec, c.op, c.nrhs, st, filter_ru, s);
 }
 
 cola_status ru_block(const SolveCtx &c, cudaStream_t s) {
     BlasArgs B = blas(c, {{V_XHI, COLA_F64}, {V_XLO, c.xprec}});
     COLA_CUDA(launch_ru_accumulate(B, false, s), "reliable update (accumulate)");
-    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, c.owner->states, true, false, s));
+    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, c.owner->states, true, s));
     B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
     COLA_CUDA(launch_ru_residual(B, s), "reliable update (residual)");
     return COLA_OK;
 }
 
 cola_status iter_head(const SolveCtx &c, cudaStream_t s) {
-    COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, true, s));
+    COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, s));
+    BlasArgs P = blas(c, {{V_MP, c.prec}});  // <p, A p> = |M p|^2, alpha
+    COLA_CUDA(launch_cg_pq(P, s), "cg <p, Ap>");
     BlasArgs B = blas(c, {{V_XLO, c.xprec}, {V_RLO, c.prec}, {V_P, c.prec}, {V_Q, c.prec}});
     COLA_CUDA(launch_cg_update_xr(B, s), "cg update x, r");
     return COLA_OK;
@@ -303,7 +306,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
     c.nrhs = prm->nrhs;
     c.nparity = prm->op == COLA_OP_EO ? 1 : 2;
     const bool dirac = prm->system == COLA_SYS_DIRAC;
-    int pstride = 0, nrows = nlat * c.nrhs;
+    int maxblocks = 0, nrows = nlat * c.nrhs;
     for (int l = 0; l < nlat; ++l) {
         cola_gauge g = gs[l];
         if (!g->links[COLA_F64]) {
@@ -339,11 +342,11 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         COLA_TRY(ws_slot(g, S_MP64, hi, &L.mp64));
         L.borig = nullptr;
         if (dirac) COLA_TRY(ws_slot(g, S_BORIG, hi, &L.borig));
-        const int blas_blocks = (G.Vh * 2 + 255) / 256;
-        const int ds_blocks = ((G.Vh + 31) / 32) * 2;
-        pstride = std::max(pstride, std::max(blas_blocks, ds_blocks));
+        const int blas_warps = (G.Vh * 2 + 255) / 256 * 8;
+        const int ds_warps = ((G.Vh + 31) / 32 + 8) * 2;  // any tuned block shape
+        maxblocks = std::max(maxblocks, std::max(blas_warps, ds_warps));
     }
-    COLA_TRY(ws_reduce(c.owner, nrows, pstride, (size_t)nrows * 2));
+    COLA_TRY(ws_reduce(c.owner, nrows, red_pstride(maxblocks), (size_t)nrows * red_cstride(maxblocks)));
     COLA_TRY(ws_states(c.owner, nrows));
     CgState *hs = c.owner->h_states;
 
@@ -361,14 +364,14 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
             if (prm->op == COLA_OP_EO) {
                 // bhat_e = b_e + kappa H_eo b_o (into mp64);  b = Mhat^dag bhat
                 DslashArgs A = make_dslash_args(g, COLA_F64, L.mp64, L.borig, L.borig, c.nrhs, 0, 1.0, k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, false, s));
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, s));
                 A = make_dslash_args(g, COLA_F64, L.t64, L.mp64, nullptr, c.nrhs, 1, 0.0, 1.0);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, false, false, s));
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, false, s));
                 A = make_dslash_args(g, COLA_F64, L.b, L.t64, L.mp64, c.nrhs, 0, 1.0, -k * k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, true, false, s));
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, true, s));
             } else {
                 DslashArgs A = make_dslash_args(g, COLA_F64, L.b, L.borig, L.borig, c.nrhs, 0, 1.0, -k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 2, true, true, false, s));
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 2, true, true, s));
             }
         }
         COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.xhi, xs[l], c.nrhs, prm->op == COLA_OP_EO ? 1 : 3, s), "pack x0");
@@ -389,7 +392,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         COLA_CUDA(launch_init_norms(B, s), "|b|^2");
     }
     // r = b - A x0 in FP64, r_lo = p = r
-    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, false, s));
+    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, s));
     {
         BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
         B.init = 1;
@@ -410,7 +413,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         // Kernels launched while a stream is capturing are not autotuned, so
         // tune the inner operator once here: q = A p is recomputed by the
         // first iteration before anything reads it.
-        COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, nullptr, false, false, s));
+        COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, nullptr, false, s));
     }
     if (running) COLA_TRY(prm->use_graph ? run_graph_loop(c, s) : run_host_loop(c, s));
     {
@@ -427,7 +430,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         if (dirac && prm->op == COLA_OP_EO) {
             // x_o = b_o + kappa H_oe x_e
             DslashArgs A = make_dslash_args(g, COLA_F64, L.xhi, L.xhi, L.borig, c.nrhs, 1, 1.0, k);
-            COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, false, s));
+            COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, s));
         }
         if (prm->op == COLA_OP_EO && !dirac) {
             const size_t pb = spinor_parity_bytes(COLA_F64, G.Vh);
@@ -441,7 +444,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         for (int l = 0; l < nlat; ++l) {
             LatCtx &L = c.lat[l];
             DslashArgs A = make_dslash_args(L.g, COLA_F64, L.ax, L.xhi, L.xhi, c.nrhs, 0, 1.0, -L.g->lat.kappa);
-            COLA_TRY(dslash_launch(L.g, COLA_F64, A, 2, false, true, false, s));
+            COLA_TRY(dslash_launch(L.g, COLA_F64, A, 2, false, true, s));
         }
         double *d_norms;
         COLA_TRY(ws_slot(c.owner, S_NORMS, 2 * nrows * sizeof(double), reinterpret_cast<void **>(&d_norms)));

@@ -180,3 +180,19 @@ def test_batched_rejects_duplicate_handles(cola):
     g = cola.Gauge(to_dev(u), dims, 0.12, BC_AP, precisions=("f64",))
     with pytest.raises(cola.ColaError, match="twice"):
         cola.cg_solve_batched([g, g], [to_dev(b), to_dev(b)])
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_eo_solve_16x16x16x32_workload(cola, inner):
+    """Even-odd D^dag D CG on 16^3x32: links exp(0.3 i H) as 12-real SU(3), kappa 0.125,
+    Gaussian source; FP64 throughout and FP32 storage, 1e-10 true residual by the oracle.
+    The launches here span many reduction groups (thousands of blocks)."""
+    dims = (16, 16, 16, 32)
+    kappa = 0.125
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(1, 0))
+    b = synth.gaussian_spinor(dims, synth.seed_for(1, 1))
+    g = cola.Gauge(to_dev(u), dims, kappa, BC_AP, precisions=("f64", "f32"), recon={"f64": 12, "f32": 12})
+    x, info = cola.cg_solve(g, to_dev(b), tol=1e-10, op="eo", inner=inner, delta=0.1, use_graph=True)
+    assert info[0].status == 0
+    r = true_resid_eo(u, x.cpu().numpy(), b, kappa, dims)
+    assert r <= 1e-10 and abs(r - info[0].true_rel_resid) < 1e-12
