@@ -43,6 +43,14 @@ METRIC = "Wilson Dslash GFLOP/s & HBM GB/s; mixed-vs-FP64 CG time at 1e-10 resid
 # algorithmic bytes per output site of one parity apply (FP16 storage, 12-real links):
 # 8 links x 24 B + input spinor 48 B + its FP32 scale + output 48 B + scale
 BYTES_PER_SITE_F16 = 8 * 24 + 52 + 52
+# FP64 peak of this part from its unit counts and clock: 152 SMs x 2 DFMA per
+# SM per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2 flop
+# x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel at
+# 32^3x64 (profiles/dslash_f64_32x32x32x64.md, profiles/dslash_f16_32x32x32x64.md);
+# None when the kernel changed after the capture.
+NCU_TRAFFIC = {"f64": None, "f16": None}
 
 
 def dist_env():
@@ -176,7 +184,7 @@ def run_cola(args):
     vh = vol // 2
 
     u, b = make_inputs(dev)
-    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f32", "f16"), recon={"f64": 18, "f32": 12, "f16": 12})
+    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f16"), recon={"f64": 18, "f16": 12})
 
     use_graph = not args.host_loop
 
@@ -220,7 +228,11 @@ def run_cola(args):
     n_ds = [4 * it + 4 * ru for it, ru in zip(iters, rus)]
     flops = sum(FLOP_PER_SITE * vh * n for n in n_ds) * world
     value = flops / (t_ms * 1e-3) / 1e9
-    launches = sum(6 + 8 * it + 6 * ru + 4 for it, ru in zip(iters, rus))
+    # kernels per solve: 15 set-up/finish launches (packing, |b|^2, initial FP64
+    # residual, autotuning pass, final accumulate, unpacking), 9 per iteration
+    # (4 Dslash, <p,Ap>, x/r update, p update, 2 graph-control kernels) and 6
+    # per reliable update after the first (accumulate, 4 FP64 Dslash, residual)
+    launches = sum(15 + 9 * it + 6 * (ru - 1) for it, ru in zip(iters, rus))
 
     # plain FP64 CG on the same inputs (the comparison of the metric)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -266,24 +278,26 @@ def run_cola(args):
 
     multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # the canonical links and the source from pinned host memory, re-packs the
+    # links into the (reused) gauge handle, solves and copies x back
     u_host = u.cpu().pin_memory()
     b_host = b.cpu().pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
-    del g
+    ud = torch.empty_like(u)
+    bd = torch.empty_like(b)
     torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 3))
     w0 = time.perf_counter()
     e2e_ds = 0
     for _ in range(e2e_steps):
-        ud = u_host.to(dev, non_blocking=True)
-        bd = b_host.to(dev, non_blocking=True)
-        ge = cola.Gauge(ud, DIMS, KAPPA, BC, precisions=("f64", "f16"), recon={"f64": 18, "f16": 12})
-        xe, ie = cola.cg_solve(ge, bd, tol=TOL, op="eo", inner="f16", delta=DELTA, use_graph=True)
+        ud.copy_(u_host, non_blocking=True)
+        bd.copy_(b_host, non_blocking=True)
+        g.update(ud)
+        xe, ie = cola.cg_solve(g, bd, tol=TOL, op="eo", inner="f16", delta=DELTA, use_graph=True)
         x_host.copy_(xe, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ds += 4 * ie[0].iters + 4 * ie[0].reliable_updates
-        del ge
     e2e_s = (time.perf_counter() - w0) / e2e_steps
     e2e_value = FLOP_PER_SITE * vh * (e2e_ds / e2e_steps) * world / e2e_s / 1e9
 
@@ -307,9 +321,19 @@ def run_cola(args):
             "dslash_f16": {"us_per_parity_apply": ds_us, "gflops": FLOP_PER_SITE * vh / (ds_us * 1e-6) / 1e9,
                            "algorithmic_gbs": achieved},
             "dslash_f64": {"us_per_parity_apply": ds64_us, "gflops": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e9},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "dslash_kernel<F16,12> parity apply",
-                         "peak_kind": f"{peak_kind} hbm_gbs (burst, kernel timed alone)"},
+            # dominant kernel by time share: the FP64 hopping term of the reliable
+            # updates (about half of the solve), bound by the FP64 pipe
+            "roofline": {"bound": "alu", "achieved": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,
+                         "traffic": NCU_TRAFFIC["f64"], "kernel": "dslash_kernel<F64,18> parity apply",
+                         "peak_kind": "FP64 peak derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2 "
+                                      "flop x 2.07 GHz); 1320 algorithmic flop per site"},
+            # the inner-iteration kernel, bound by HBM
+            "roofline_inner": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": achieved / peak, "traffic": NCU_TRAFFIC["f16"],
+                               "kernel": "dslash_kernel<F16,12> parity apply",
+                               "peak_kind": f"{peak_kind} hbm_gbs (burst, kernel timed alone)"},
             "e2e": {"value": e2e_value, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": u_host.numel() * 16 + b_host.numel() * 16,
                     "d2h_bytes_per_step": x_host.numel() * 16, "ms_per_step": e2e_s * 1e3},

@@ -87,6 +87,10 @@ cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev,
                               const cola_gauge_opts *opts, cudaStream_t stream,
                               cola_gauge *out);
 cola_status cola_gauge_destroy(cola_gauge g);
+/* Re-pack new links (same lattice, same layout as cola_gauge_create) into an
+ * existing handle, keeping its precisions, reconstruction and workspace (an
+ * HMC trajectory changes the links at every step). */
+cola_status cola_gauge_update(cola_gauge g, const void *links_dev, cudaStream_t stream);
 
 /* Bytes of one packed spinor field (both parities) times nrhs. */
 size_t cola_spinor_bytes(const cola_lattice *lat, cola_prec prec, int nrhs);

@@ -58,6 +58,7 @@ _st = ctypes.c_int
 SIGNATURES = {
     "cola_gauge_create": (_st, [ctypes.POINTER(Lattice), _vp, ctypes.POINTER(GaugeOpts), _vp, ctypes.POINTER(_vp)]),
     "cola_gauge_destroy": (_st, [_vp]),
+    "cola_gauge_update": (_st, [_vp, _vp, _vp]),
     "cola_spinor_bytes": (ctypes.c_size_t, [ctypes.POINTER(Lattice), _i, _i]),
     "cola_spinor_pack": (_st, [_vp, _vp, _vp, _i, _i, _vp]),
     "cola_spinor_unpack": (_st, [_vp, _vp, _vp, _i, _i, _vp]),

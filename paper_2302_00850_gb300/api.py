@@ -81,6 +81,11 @@ class Gauge:
         check(self.lib.cola_gauge_create(ctypes.byref(self.lat), _complex_field(links, 4 * self.volume * 9, "links"),
                                          ctypes.byref(opts), _stream(self.device), ctypes.byref(self.handle)))
 
+    def update(self, links):
+        """Re-pack new links (same lattice) into this handle, keeping its workspace."""
+        check(self.lib.cola_gauge_update(self.handle, _complex_field(links, 4 * self.volume * 9, "links"),
+                                         _stream(self.device)))
+
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             self.lib.cola_gauge_destroy(self.handle)

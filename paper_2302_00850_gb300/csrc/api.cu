@@ -256,6 +256,15 @@ cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev, co
     return COLA_OK;
 }
 
+cola_status cola_gauge_update(cola_gauge g, const void *links_dev, cudaStream_t stream) {
+    if (!g || !links_dev) return arg_error("null argument to cola_gauge_update");
+    for (int p = 0; p < 3; ++p)
+        if (g->links[p])
+            COLA_TRY(cuda_check(launch_pack_gauge(p, g->recon[p], g->geom, g->links[p], links_dev, stream),
+                                "link packing"));
+    return COLA_OK;
+}
+
 cola_status cola_gauge_destroy(cola_gauge g) {
     if (!g) return COLA_OK;
     cudaDeviceSynchronize();

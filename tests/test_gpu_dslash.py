@@ -172,3 +172,14 @@ def test_full_size_sampled_sites(cola, big, prec):
                             rng.integers(0, v, 4000)])
     want = oracle.hop_sites(u, psi, BC_AP, sites)
     assert rel_err(got[sites], want) < TOL[prec]
+
+
+def test_gauge_update_repacks_links(cola):
+    dims = (4, 6, 2, 8)
+    u1, psi = lattice_inputs(dims, config=56)
+    u2 = synth.gauge_field(dims, 0.3, synth.seed_for(57, 0))
+    g = make_gauge(cola, u1, dims)
+    g.update(to_dev(u2))
+    for prec in ("f64", "f32", "f16"):
+        got = cola.apply_dirac(g, to_dev(psi), prec=prec).cpu().numpy()
+        assert rel_err(got, oracle.dirac(u2, psi, 0.124, BC_AP)) < TOL[prec]
