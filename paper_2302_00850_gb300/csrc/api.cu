@@ -64,6 +64,9 @@ static Geom make_geom(const cola_lattice &lat) {
         g.bc[m][1] = lat.bc[m][1];
         g.bc_trivial[m] = (lat.bc[m][0] == 1.0 && lat.bc[m][1] == 0.0);
     }
+    g.div_xh = make_fastdiv(g.Lxh);
+    g.div_y = make_fastdiv(g.L[1]);
+    g.div_z = make_fastdiv(g.L[2]);
     return g;
 }
 

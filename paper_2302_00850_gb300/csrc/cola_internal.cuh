@@ -12,6 +12,35 @@
 namespace cola {
 
 // ---------------------------------------------------------------- geometry --
+// Division by a fixed divisor d through a multiply-high (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l for 0 <= n < 2^31.
+struct FastDiv {
+    unsigned m, l;
+    __host__ __device__ __forceinline__ int div(int n) const {
+        return (int)((__umulhi_host_dev((unsigned)n, m) + (unsigned)n) >> l);
+    }
+    static __host__ __device__ __forceinline__ unsigned __umulhi_host_dev(unsigned a, unsigned b) {
+#ifdef __CUDA_ARCH__
+        return __umulhi(a, b);
+#else
+        return (unsigned)(((unsigned long long)a * b) >> 32);
+#endif
+    }
+};
+
+inline FastDiv make_fastdiv(int d) {
+    FastDiv f{0u, 0u};
+    if (d > 1) {
+        unsigned l = 0;
+        while ((1ull << l) < (unsigned long long)d) ++l;
+        f.l = l;
+        f.m = (unsigned)((((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d) + 1ull);
+    }
+    return f;
+}
+
 // Per-lattice constants passed by value to every kernel.
 struct Geom {
     int L[4];        // Lx, Ly, Lz, Lt
@@ -21,6 +50,7 @@ struct Geom {
     int stride[4];   // checkerboard-index offset of a +1 step in y, z, t (x unused)
     double bc[4][2]; // boundary phase per direction
     int bc_trivial[4];
+    FastDiv div_xh, div_y, div_z;  // by Lxh, Ly, Lz
 };
 
 // Site coordinates of checkerboard index cb on parity `par`.
@@ -30,12 +60,12 @@ struct Coord {
 
 __device__ __forceinline__ Coord cb_coord(const Geom &g, int cb, int par) {
     Coord c;
-    int xh = cb % g.Lxh;
-    int r = cb / g.Lxh;
-    c.y = r % g.L[1];
-    r /= g.L[1];
-    c.z = r % g.L[2];
-    c.t = r / g.L[2];
+    const int r1 = g.div_xh.div(cb);
+    const int xh = cb - r1 * g.Lxh;
+    const int r2 = g.div_y.div(r1);
+    c.y = r1 - r2 * g.L[1];
+    c.t = g.div_z.div(r2);
+    c.z = r2 - c.t * g.L[2];
     c.x = 2 * xh + ((par + c.y + c.z + c.t) & 1);
     return c;
 }

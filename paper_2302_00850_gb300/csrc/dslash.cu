@@ -227,11 +227,16 @@ struct HopLayout {
     static constexpr int bytes = spin16 * 16 + scale4 * 4 + link_chunks * link_bytes;
 };
 
+// The staged kernel always runs kStagedThreads threads per block (sites x
+// right-hand sides), so every shared-memory offset is a compile-time constant
+// plus one per-thread term.
+constexpr int kStagedThreads = 128;
+
 template <int P, int RECON>
 struct Stage {
     using L = HopLayout<P, RECON>;
+    static constexpr int T = kStagedThreads;
     char *base;  // this stage's area
-    int T;       // threads per block
     __device__ uint4 *spin(int k, int tid) const { return reinterpret_cast<uint4 *>(base) + k * T + tid; }
     __device__ float *scale(int tid) const {
         return reinterpret_cast<float *>(base + L::spin16 * 16 * T) + tid;
@@ -331,12 +336,12 @@ __device__ __forceinline__ void staged_step(const DslashLat &A, const Coord &c, 
                                             Cx<float> (&acc)[12]) {
     using L = HopLayout<P, RECON>;
     if constexpr (J + NS - 1 < 8) {
-        Stage<P, RECON> nx{smem + ((J + NS - 1) % NS) * L::bytes * T, T};
+        Stage<P, RECON> nx{smem + ((J + NS - 1) % NS) * L::bytes * kStagedThreads};
         stage_issue<P, RECON, J + NS - 1>(A, c, cb, in, lo, li, nx, tid);
     }
     cp_async_commit();
     cp_async_wait<NS - 1>();
-    Stage<P, RECON> cur{smem + (J % NS) * L::bytes * T, T};
+    Stage<P, RECON> cur{smem + (J % NS) * L::bytes * kStagedThreads};
     stage_compute<P, RECON, J, DAGGER>(A, c, cur, tid, acc);
     if constexpr (J < 7) staged_step<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid, acc);
 }
@@ -346,7 +351,7 @@ __device__ __forceinline__ void staged_prologue(const DslashLat &A, const Coord 
                                                 const char *lo, const char *li, char *smem, int T, int tid) {
     using L = HopLayout<P, RECON>;
     if constexpr (J < NS - 1) {
-        Stage<P, RECON> st{smem + J * L::bytes * T, T};
+        Stage<P, RECON> st{smem + J * L::bytes * kStagedThreads};
         stage_issue<P, RECON, J>(A, c, cb, in, lo, li, st, tid);
         cp_async_commit();
         staged_prologue<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid);
@@ -357,7 +362,7 @@ template <int P, int RECON, bool DAGGER, int NS>
 __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, int cb, const char *in,
                                             const char *lo, const char *li, Cx<float> (&acc)[12]) {
     extern __shared__ __align__(16) char smem_dyn[];
-    const int T = blockDim.x * blockDim.y;
+    constexpr int T = kStagedThreads;  // blockDim.x * blockDim.y, enforced by launch_dslash
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     staged_prologue<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid);
     staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc);
@@ -591,10 +596,12 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
     }
     const int bys[] = {1, 2, 4, 8};
     const int bxs[] = {32, 64, 128, 256};
+    const bool staged = prec != COLA_F64 && staged_depth(prec) > 0;
     for (int by : bys) {
         if (by > A0.nrhs) continue;
         for (int bx : bxs) {
             if (bx * by > 256 || bx * by < 64) continue;
+            if (staged && bx * by != kStagedThreads) continue;
             DslashArgs A = A0;
             A.rhs_per_block = by;
             A.state = nullptr;
@@ -639,6 +646,11 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
                 A.rhs_per_block = it->second.by;
             }
         }
+    }
+    if (prec != COLA_F64 && staged_depth(prec) > 0 && block_x * A.rhs_per_block != kStagedThreads) {
+        // the staged kernel's shared-memory layout is built for kStagedThreads threads
+        A.rhs_per_block = std::min(A.rhs_per_block, 4);
+        block_x = kStagedThreads / A.rhs_per_block;
     }
     return launch_now(prec, recon, A, nparity, dagger, xpay, block_x, s);
 }
