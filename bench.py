@@ -228,11 +228,13 @@ def run_cola(args):
     n_ds = [4 * it + 4 * ru for it, ru in zip(iters, rus)]
     flops = sum(FLOP_PER_SITE * vh * n for n in n_ds) * world
     value = flops / (t_ms * 1e-3) / 1e9
-    # kernels per solve: 15 set-up/finish launches (packing, |b|^2, initial FP64
-    # residual, autotuning pass, final accumulate, unpacking), 9 per iteration
-    # (4 Dslash, <p,Ap>, x/r update, p update, 2 graph-control kernels) and 6
-    # per reliable update after the first (accumulate, 4 FP64 Dslash, residual)
-    launches = sum(15 + 9 * it + 6 * (ru - 1) for it, ru in zip(iters, rus))
+    # kernels per solve: 9 set-up/finish launches (packing, |b|^2 and its
+    # finishing kernel, the zero-guess check, initial residual and finisher,
+    # final accumulate, unpacking), 11 per iteration (4 Dslash, <p,Ap> and
+    # x/r update each with a finishing kernel, p update, 2 graph-control
+    # kernels) and 7 per reliable update after the first (accumulate, 4 FP64
+    # Dslash, residual and its finishing kernel)
+    launches = sum(9 + 11 * it + 7 * (ru - 1) for it, ru in zip(iters, rus))
 
     # plain FP64 CG on the same inputs (the comparison of the metric)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

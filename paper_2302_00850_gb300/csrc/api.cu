@@ -91,7 +91,7 @@ cola_status ws_slot(cola_gauge g, int k, size_t bytes, void **out) {
     return COLA_OK;
 }
 
-cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride, size_t ncounters) {
+cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride) {
     const size_t need = nrows * pstride;
     if (g->partials_count < need) {
         if (g->partials) cudaFree(g->partials);
@@ -99,15 +99,6 @@ cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride, size_t ncounte
         g->partials_count = 0;
         COLA_CUDA(cudaMalloc(&g->partials, need * sizeof(double)), "reduction scratch");
         g->partials_count = need;
-    }
-    const size_t nc = ncounters > nrows ? ncounters : nrows;
-    if (g->counters_count < nc) {
-        if (g->counters) cudaFree(g->counters);
-        g->counters = nullptr;
-        g->counters_count = 0;
-        COLA_CUDA(cudaMalloc(&g->counters, nc * sizeof(unsigned)), "reduction counters");
-        COLA_CUDA(cudaMemset(g->counters, 0, nc * sizeof(unsigned)), "reduction counters");
-        g->counters_count = nc;
     }
     return COLA_OK;
 }
@@ -276,7 +267,6 @@ cola_status cola_gauge_destroy(cola_gauge g) {
     for (int k = 0; k < cola_gauge_s::kSlots; ++k)
         if (g->slot[k]) cudaFree(g->slot[k]);
     if (g->partials) cudaFree(g->partials);
-    if (g->counters) cudaFree(g->counters);
     if (g->states) cudaFree(g->states);
     if (g->h_states) cudaFreeHost(g->h_states);
     delete g;

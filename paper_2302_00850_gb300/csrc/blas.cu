@@ -2,17 +2,21 @@
 //
 // The paper's benchmark solver uses 32-bit inner iterations and a 64-bit outer
 // solver (its Fig. 2 discussion, after Clark et al.).  Here every CG scalar
-// (alpha, beta, |r|^2, <p, Ap>) is reduced in FP64 on the device, in a fixed
-// block order so repeated solves give identical results, and each update
-// kernel also produces the next reduction so that one pass over the vectors
-// does both.  The last block of each row's reduction makes the solver's
-// decisions (reliable update due, converged, iteration cap, breakdown) in
-// CgState.  Every kernel walks one table of lattices (a batch of up to
-// kMaxBatch lattices, each with nrhs right-hand sides), so a batch of uneven
-// lattices is one launch per step.
+// (alpha, beta, |r|^2, <p, Ap>) is reduced in FP64 on the device, and each
+// update kernel also produces the next reduction so that one pass over the
+// vectors does both.  Reductions are deterministic: each block writes one
+// partial per row with a plain store, then a finishing kernel with one block
+// per row sums the partials in block order and makes the solver's decisions
+// (reliable update due, converged, iteration cap, breakdown) in CgState.  No
+// floating-point atomics and no memory fences are involved, so repeated
+// solves give identical results.  Every kernel walks one table of lattices
+// (a batch of up to kMaxBatch lattices, each with nrhs right-hand sides), so
+// a batch of uneven lattices is one launch per step.
 #include "cola_impl.h"
 
 namespace cola {
+
+static constexpr int kBlasBlock = 256;
 
 // Site s of lattice l (s in [0, nparity * vh)) -> parity and checkerboard index.
 struct SiteRef {
@@ -59,24 +63,23 @@ __device__ __forceinline__ double site_norm2(const Cx<R> (&s)[12]) {
     return (double)a;
 }
 
-// Warp-granular grid reduction of one row (every warp of the launch takes part).
-__device__ __forceinline__ bool blas_reduce(const BlasArgs &B, const SiteRef &r, double v, double *tot) {
-    const int wpb = blockDim.x >> 5;
-    return reduce_warp_rows(v, B.partials, B.pstride, r.row, B.counters + (size_t)r.row * B.cstride,
-                            B.lat[r.l].nblocks * wpb, r.bid * wpb + (threadIdx.x >> 5), tot);
+// The block's partial of its row (every thread of the block takes part).
+__device__ __forceinline__ void write_partial(const BlasArgs &B, const SiteRef &r, double v) {
+    __shared__ double sh[kBlasBlock / 32];
+    const double t = block_sum(v, sh);
+    if (threadIdx.x == 0) B.partials[(size_t)r.row * B.pstride + r.bid] = t;
 }
 
 // ---------------------------------------------------------------------------
-// slots (x, r, p, q):  x += alpha p;  r -= alpha q;  rho_new = |r|^2
+// slots (x, r, p, q):  x += alpha p;  r -= alpha q;  partial |r|^2
 template <int PX, int PV>
-__global__ void __launch_bounds__(256) cg_update_xr_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) cg_update_xr_kernel(const __grid_constant__ BlasArgs B) {
     using RV = typename Prec<PV>::real;
     using RX = typename Prec<PX>::real;
     const SiteRef r = blas_site(B);
-    CgState &S = B.state[r.row];
-    const bool live = !S.done;
+    const CgState &S = B.state[r.row];
     double nr = 0.0;
-    if (live && r.ok) {
+    if (!S.done && r.ok) {
         const double alpha = S.alpha;
         const int vh = B.lat[r.l].vh;
         Cx<RV> pv[12], qv[12], rv[12];
@@ -98,24 +101,12 @@ __global__ void __launch_bounds__(256) cg_update_xr_kernel(const __grid_constant
         SpinorIO<PV>::store(vptr_w(B, r, 1), vh, r.cb, rv);
         nr = site_norm2(rv);
     }
-    double tot;
-    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
-        {
-            S.rho_new = tot;
-            S.iter += 1;
-            if (!isfinite(tot)) {
-                S.status = COLA_ERR_BREAKDOWN;
-                S.done = 1;
-            } else {
-                S.ru = (tot < S.delta2 * S.r2_last) || (tot <= S.tol2) || (S.iter >= S.max_iter);
-            }
-        }
-    }
+    write_partial(B, r, nr);
 }
 
 // slots (p, r):  p = r + beta p,  beta = rho_new / rho
 template <int PV>
-__global__ void __launch_bounds__(256) cg_update_p_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) cg_update_p_kernel(const __grid_constant__ BlasArgs B) {
     using RV = typename Prec<PV>::real;
     const SiteRef r = blas_site(B);
     const CgState &S = B.state[r.row];
@@ -133,33 +124,22 @@ __global__ void __launch_bounds__(256) cg_update_p_kernel(const __grid_constant_
     SpinorIO<PV>::store(vptr_w(B, r, 0), vh, r.cb, pv);
 }
 
-// slot (mp):  pq = |M p|^2 = <p, A p>;  rho = rho_new;  alpha = rho / pq
+// slot (mp):  partial |M p|^2 = <p, A p>
 template <int PV>
-__global__ void __launch_bounds__(256) cg_pq_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) cg_pq_kernel(const __grid_constant__ BlasArgs B) {
     const SiteRef r = blas_site(B);
-    CgState &S = B.state[r.row];
-    const bool live = !S.done;
     double nr = 0.0;
-    if (live && r.ok) {
+    if (!B.state[r.row].done && r.ok) {
         Cx<typename Prec<PV>::real> m[12];
         SpinorIO<PV>::load(vptr(B, r, 0), B.lat[r.l].vh, r.cb, m);
         nr = site_norm2(m);
     }
-    double tot;
-    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
-        S.pq = tot;
-        S.rho = S.rho_new;
-        S.alpha = S.rho / tot;
-        if (!(tot > 0.0) || !isfinite(S.alpha)) {
-            S.status = COLA_ERR_BREAKDOWN;
-            S.done = 1;
-        }
-    }
+    write_partial(B, r, nr);
 }
 
 // slots (x_hi, x_lo):  x_hi += x_lo;  x_lo = 0
 template <int PX>
-__global__ void __launch_bounds__(256) ru_accumulate_kernel(const __grid_constant__ BlasArgs B, int force) {
+__global__ void __launch_bounds__(kBlasBlock) ru_accumulate_kernel(const __grid_constant__ BlasArgs B, int force) {
     using RX = typename Prec<PX>::real;
     const SiteRef r = blas_site(B);
     const CgState &S = B.state[r.row];
@@ -179,15 +159,16 @@ __global__ void __launch_bounds__(256) ru_accumulate_kernel(const __grid_constan
     SpinorIO<PX>::store(vptr_w(B, r, 1), vh, r.cb, xl);
 }
 
-// slots (r_hi, b, ax, r_lo, p):  r_hi = b - ax;  r_lo = r_hi;  (init: p = r_lo)
-// |r_hi|^2 -> r2_last, rho_new; converged / cap / breakdown decisions.
+__device__ __forceinline__ bool ru_live(const BlasArgs &B, const CgState &S) {
+    return B.init ? true : (S.ru && !S.done);
+}
+
+// slots (r_hi, b, ax, r_lo, p):  r_hi = b - ax;  r_lo = r_hi;  (init: p = r_lo);  partial |r_hi|^2
 template <int PV>
-__global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) ru_residual_kernel(const __grid_constant__ BlasArgs B) {
     const SiteRef r = blas_site(B);
-    CgState &S = B.state[r.row];
-    const bool live = B.init ? true : (S.ru && !S.done);
     double nr = 0.0;
-    if (live && r.ok) {
+    if (ru_live(B, B.state[r.row]) && r.ok) {
         const int vh = B.lat[r.l].vh;
         Cx<double> bv[12], av[12];
         SpinorIO<COLA_F64>::load(vptr(B, r, 1), vh, r.cb, bv);
@@ -204,9 +185,74 @@ __global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant_
         if (B.init) SpinorIO<PV>::store(vptr_w(B, r, 4), vh, r.cb, lv);
         nr = site_norm2(bv);
     }
-    double tot;
-    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0 && live) {
-        {
+    write_partial(B, r, nr);
+}
+
+// slot (v):  partial |v|^2
+template <int P>
+__global__ void __launch_bounds__(kBlasBlock) norm2_kernel(const __grid_constant__ BlasArgs B) {
+    const SiteRef r = blas_site(B);
+    double nr = 0.0;
+    if (r.ok) {
+        Cx<typename Prec<P>::real> a[12];
+        SpinorIO<P>::load(vptr(B, r, 0), B.lat[r.l].vh, r.cb, a);
+        nr = site_norm2(a);
+    }
+    write_partial(B, r, nr);
+}
+
+// ------------------------------------------------------------- finishing --
+enum FinishMode { FIN_XR, FIN_PQ, FIN_RU, FIN_NORM, FIN_INIT };
+
+// One block per row: sum the row's block partials in block order, then decide.
+template <int MODE>
+__global__ void __launch_bounds__(512) finish_kernel(const __grid_constant__ BlasArgs B) {
+    __shared__ double sh[512 / 32];
+    const int row = blockIdx.x;
+    const int l = row / B.nrhs;  // rows are lattice-major
+    const int nb = B.lat[l].nblocks;
+    const double *part = B.partials + (size_t)row * B.pstride;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int b = threadIdx.x;
+    for (; b + 3 * (int)blockDim.x < nb; b += 4 * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] += part[b + k * blockDim.x];
+    }
+    for (; b < nb; b += blockDim.x) a[0] += part[b];
+    const double tot = block_sum((a[0] + a[1]) + (a[2] + a[3]), sh);
+    if (threadIdx.x != 0) return;
+    if constexpr (MODE == FIN_NORM) {
+        B.out[row] = tot;
+    } else {
+        CgState &S = B.state[row];
+        if constexpr (MODE == FIN_INIT) {
+            S.b2 = tot;
+            S.tol2 = S.tol2 * tot;  // tol2 holds tol^2 on entry
+            if (tot == 0.0) {
+                S.done = 1;
+                S.status = COLA_OK;
+            }
+        } else if constexpr (MODE == FIN_PQ) {
+            if (S.done) return;
+            S.pq = tot;
+            S.rho = S.rho_new;
+            S.alpha = S.rho / tot;
+            if (!(tot > 0.0) || !isfinite(S.alpha)) {
+                S.status = COLA_ERR_BREAKDOWN;
+                S.done = 1;
+            }
+        } else if constexpr (MODE == FIN_XR) {
+            if (S.done) return;
+            S.rho_new = tot;
+            S.iter += 1;
+            if (!isfinite(tot)) {
+                S.status = COLA_ERR_BREAKDOWN;
+                S.done = 1;
+            } else {
+                S.ru = (tot < S.delta2 * S.r2_last) || (tot <= S.tol2) || (S.iter >= S.max_iter);
+            }
+        } else {  // FIN_RU
+            if (!ru_live(B, S)) return;
             S.rho_new = tot;
             S.r2_last = tot;
             S.ru = 0;
@@ -225,36 +271,26 @@ __global__ void __launch_bounds__(256) ru_residual_kernel(const __grid_constant_
     }
 }
 
-// slot (v):  |v|^2 per row; with init_norms, b2 and tol2 of the state.
-template <int P>
-__global__ void __launch_bounds__(256) norm2_kernel(const __grid_constant__ BlasArgs B, int init_norms) {
+// slot (v):  flags[row] |= 1 if any stored bit of the row's field is nonzero
+// (an initial guess of exactly zero lets the solver skip A x0).
+__global__ void __launch_bounds__(kBlasBlock) any_nonzero_kernel(const __grid_constant__ BlasArgs B, unsigned *flags) {
     const SiteRef r = blas_site(B);
-    double nr = 0.0;
+    bool nz = false;
     if (r.ok) {
-        Cx<typename Prec<P>::real> a[12];
-        SpinorIO<P>::load(vptr(B, r, 0), B.lat[r.l].vh, r.cb, a);
-        nr = site_norm2(a);
-    }
-    double tot;
-    if (blas_reduce(B, r, nr, &tot) && (threadIdx.x & 31) == 0) {
-        {
-            if (B.out) B.out[r.row] = tot;
-            if (init_norms) {
-                CgState &S = B.state[r.row];
-                S.b2 = tot;
-                S.tol2 = S.tol2 * tot;  // tol2 holds tol^2 on entry
-                if (tot == 0.0) {
-                    S.done = 1;
-                    S.status = COLA_OK;
-                }
-            }
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(vptr(B, r, 0));
+        const int vh = B.lat[r.l].vh;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const ulonglong2 v = __ldg(p + (size_t)c * vh + r.cb);
+            nz |= ((v.x | v.y) << 1) != 0;  // -0.0 counts as zero
         }
     }
+    if (__any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) atomicOr(flags + r.row, 1u);
 }
 
 // slots (dst, src)
 template <int PD, int PS>
-__global__ void __launch_bounds__(256) convert_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) convert_kernel(const __grid_constant__ BlasArgs B) {
     const SiteRef r = blas_site(B);
     if (!r.ok) return;
     const int vh = B.lat[r.l].vh;
@@ -267,7 +303,7 @@ __global__ void __launch_bounds__(256) convert_kernel(const __grid_constant__ Bl
 
 // slots (dst, x, y):  dst = a x + b y (one precision)
 template <int P>
-__global__ void __launch_bounds__(256) axpby_kernel(const __grid_constant__ BlasArgs B) {
+__global__ void __launch_bounds__(kBlasBlock) axpby_kernel(const __grid_constant__ BlasArgs B) {
     using R = typename Prec<P>::real;
     const SiteRef r = blas_site(B);
     if (!r.ok) return;
@@ -284,8 +320,6 @@ __global__ void __launch_bounds__(256) axpby_kernel(const __grid_constant__ Blas
 }
 
 // ------------------------------------------------------------------ launch --
-static constexpr int kBlasBlock = 256;
-
 static dim3 blas_grid(BlasArgs &B) {
     int total = 0;
     for (int l = 0; l < B.nlat; ++l) {
@@ -296,13 +330,19 @@ static dim3 blas_grid(BlasArgs &B) {
     return dim3(total, B.nrhs);
 }
 
-int blas_max_warps(const BlasArgs &B) {
+int blas_max_blocks(const BlasArgs &B) {
     int mx = 0;
     for (int l = 0; l < B.nlat; ++l) {
         const int nb = (B.lat[l].vh * B.nparity + kBlasBlock - 1) / kBlasBlock;
         if (nb > mx) mx = nb;
     }
-    return mx * (kBlasBlock / 32);
+    return mx;
+}
+
+template <int MODE>
+static cudaError_t finish(const BlasArgs &B, cudaStream_t s) {
+    finish_kernel<MODE><<<B.nlat * B.nrhs, 512, 0, s>>>(B);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s) {
@@ -310,7 +350,8 @@ cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s) {
     if (B.prec[1] == COLA_F64) cg_update_xr_kernel<COLA_F64, COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
     else if (B.prec[1] == COLA_F32) cg_update_xr_kernel<COLA_F32, COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
     else cg_update_xr_kernel<COLA_F32, COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : finish<FIN_XR>(B, s);
 }
 
 cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s) {
@@ -326,7 +367,8 @@ cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s) {
     if (B.prec[0] == COLA_F64) cg_pq_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
     else if (B.prec[0] == COLA_F32) cg_pq_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
     else cg_pq_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : finish<FIN_PQ>(B, s);
 }
 
 cudaError_t launch_ru_accumulate(BlasArgs &B, bool force, cudaStream_t s) {
@@ -341,20 +383,29 @@ cudaError_t launch_ru_residual(BlasArgs &B, cudaStream_t s) {
     if (B.prec[3] == COLA_F64) ru_residual_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
     else if (B.prec[3] == COLA_F32) ru_residual_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
     else ru_residual_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : finish<FIN_RU>(B, s);
 }
 
 cudaError_t launch_init_norms(BlasArgs &B, cudaStream_t s) {
     const dim3 g = blas_grid(B);
-    norm2_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B, 1);
-    return cudaGetLastError();
+    norm2_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : finish<FIN_INIT>(B, s);
 }
 
 cudaError_t launch_norm2(BlasArgs &B, cudaStream_t s) {
     const dim3 g = blas_grid(B);
-    if (B.prec[0] == COLA_F64) norm2_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B, 0);
-    else if (B.prec[0] == COLA_F32) norm2_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B, 0);
-    else norm2_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B, 0);
+    if (B.prec[0] == COLA_F64) norm2_kernel<COLA_F64><<<g, kBlasBlock, 0, s>>>(B);
+    else if (B.prec[0] == COLA_F32) norm2_kernel<COLA_F32><<<g, kBlasBlock, 0, s>>>(B);
+    else norm2_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : finish<FIN_NORM>(B, s);
+}
+
+cudaError_t launch_any_nonzero(BlasArgs &B, unsigned *flags, cudaStream_t s) {
+    if (B.prec[0] != COLA_F64) return cudaErrorInvalidValue;
+    any_nonzero_kernel<<<blas_grid(B), kBlasBlock, 0, s>>>(B, flags);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,12 @@ struct DslashArgs {
 };
 
 int default_dslash_block(int prec, int rhs_per_block);
+// Within this scope (per thread), launch_dslash only autotunes configurations
+// it has not seen and launches nothing else.
+struct TuneOnlyScope {
+    TuneOnlyScope();
+    ~TuneOnlyScope();
+};
 // Fills block0/nblocks of every lattice and launches; block_x <= 0 picks the
 // autotuned (or default) launch shape.
 cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
@@ -76,10 +82,8 @@ struct BlasArgs {
     int prec[kMaxVecs];
     BlasLat lat[kMaxBatch];
     CgState *state;
-    double *partials;
+    double *partials;     // [row][pstride] block partials of reductions
     int pstride;
-    unsigned *counters;   // [row][cstride]
-    int cstride;
     double *out;          // norm2 results per row
     double a, b;          // axpby coefficients
     int init;             // ru_residual: initial residual (every row, also writes p)
@@ -95,9 +99,10 @@ cudaError_t launch_ru_residual(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_init_norms(BlasArgs &B, cudaStream_t s);   // st.b2 = |b|^2, st.tol2 *= |b|^2
 cudaError_t launch_norm2(BlasArgs &B, cudaStream_t s);        // out[row] = |v|^2
 cudaError_t launch_convert(BlasArgs &B, cudaStream_t s);
+cudaError_t launch_any_nonzero(BlasArgs &B, unsigned *flags, cudaStream_t s);  // F64 slot (v); flags zeroed by caller
 cudaError_t launch_axpby(BlasArgs &B, cudaStream_t s);
-// Largest warp count per row of the batched vector kernels.
-int blas_max_warps(const BlasArgs &B);
+// Largest block count per row of the batched vector kernels (partials stride).
+int blas_max_blocks(const BlasArgs &B);
 
 // ----------------------------------------------------------------- force --
 cudaError_t launch_force(const Geom &g, double kappa, const void *links_f64, int recon, double *force,
@@ -126,8 +131,6 @@ struct cola_gauge_s {
     size_t slot_bytes[kSlots] = {};
     double *partials = nullptr;
     size_t partials_count = 0;
-    unsigned *counters = nullptr;
-    size_t counters_count = 0;
     cola::CgState *states = nullptr;   // device
     cola::CgState *h_states = nullptr; // pinned host mirror
     int states_count = 0;
@@ -136,8 +139,8 @@ struct cola_gauge_s {
 namespace cola {
 // Device buffer of at least `bytes` in workspace slot `k` (grown if needed).
 cola_status ws_slot(cola_gauge g, int k, size_t bytes, void **out);
-// Reduction scratch: nrows rows of pstride partials and ncounters counters.
-cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride, size_t ncounters);
+// Reduction scratch: nrows rows of pstride block partials.
+cola_status ws_reduce(cola_gauge g, size_t nrows, size_t pstride);
 cola_status ws_states(cola_gauge g, int n);
 
 // One lattice of an operator application: out = M^dag M in with temporaries

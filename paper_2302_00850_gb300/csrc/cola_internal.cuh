@@ -352,32 +352,6 @@ struct LinkIO<COLA_F16, RECON> {
     }
 };
 
-// ------------------------------------------------------------- reductions --
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the block in a fixed order; the result is valid in thread 0.
-// `sh` must hold at least 32 doubles.
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int nthreads = blockDim.x * blockDim.y;
-    const int lane = tid & 31, warp = tid >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (warp == 0) {
-        const int nw = (nthreads + 31) >> 5;
-        r = lane < nw ? sh[lane] : 0.0;
-        r = warp_sum(r);
-    }
-    return r;
-}
-
 }  // namespace cola
 
 namespace cola {
@@ -402,25 +376,11 @@ struct CgState {
     int status;
 };
 
-// Deterministic two-level grid reduction at warp granularity (no
-// floating-point atomics, no block barriers).  Every warp of a row writes
-// its sum to part[row][warp_id]; warps are grouped kRedGroup at a time and
-// the last warp of a group to arrive (atomic ticket on the group's counter)
-// sums the group's partials in warp order into part[row][nwarps + group]; the
-// last group to finish sums those in group order.  Loads use ld.global.cg
-// (the partials come from other SMs, so L1 is bypassed).  Because no warp
-// waits for the other warps of its block, a reducing kernel runs as fast as
-// its non-reducing twin apart from the final few L2 round trips.
-// Scratch per row: part needs red_pstride(nwarps) doubles, counters
-// red_cstride(nwarps) (cnt[0] final, cnt[1 + g] group g).  Counters are reset
-// by their last user, so they are zero between launches.
-// Returns true in the lanes of the warp that finished the row; *out then
-// holds the row's sum (all lanes).
-constexpr int kRedGroup = 32;
-
-__host__ __device__ constexpr int red_groups(int nwarps) { return (nwarps + kRedGroup - 1) / kRedGroup; }
-__host__ __device__ constexpr int red_pstride(int nwarps) { return nwarps + red_groups(nwarps); }
-__host__ __device__ constexpr int red_cstride(int nwarps) { return 1 + red_groups(nwarps); }
+// Deterministic grid reductions (no floating-point atomics, no fences):
+// every block of a reducing vector kernel writes one partial per row with a
+// plain store, and a one-block-per-row finishing kernel sums those partials
+// in block order and applies the solver's decision.  The kernel boundary
+// orders the partial stores before the finisher reads them.
 
 __device__ __forceinline__ double warp_allsum(double v) {
 #pragma unroll
@@ -428,53 +388,17 @@ __device__ __forceinline__ double warp_allsum(double v) {
     return v;
 }
 
-// Sum of p[0..n) in a fixed order across one warp (eight loads in flight per lane).
-__device__ __forceinline__ double warp_sum_of(const double *p, int n) {
-    const int lane = threadIdx.x & 31;
-    double acc = 0.0;
-    for (int base = 0; base < n; base += 256) {
-        double a[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int b = base + lane + 32 * k;
-            a[k] = b < n ? __ldcg(p + b) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc += a[k];
-    }
-    return warp_allsum(acc);
-}
-
-__device__ __forceinline__ bool reduce_warp_rows(double v, double *partials, int pstride, int row, unsigned *cnt,
-                                                 int nwarps, int warp_id, double *out) {
-    const int lane = threadIdx.x & 31;
-    double *part = partials + (size_t)row * pstride;
-    const double s = warp_allsum(v);
-    const int grp = warp_id / kRedGroup;
-    const int gsize = min(kRedGroup, nwarps - grp * kRedGroup);
-    const int ngrp = red_groups(nwarps);
-    unsigned ticket = 0;
-    if (lane == 0) {
-        part[warp_id] = s;
-        __threadfence();
-        ticket = atomicAdd(cnt + 1 + grp, 1u);
-        __threadfence();
-    }
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket != (unsigned)gsize - 1) return false;
-    const double gs = warp_sum_of(part + grp * kRedGroup, gsize);
-    if (lane == 0) {
-        part[nwarps + grp] = gs;
-        cnt[1 + grp] = 0u;
-        __threadfence();
-        ticket = atomicAdd(cnt, 1u);
-        __threadfence();
-    }
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket != (unsigned)ngrp - 1) return false;
-    *out = warp_sum_of(part + nwarps, ngrp);
-    if (lane == 0) cnt[0] = 0u;
-    return true;
+// Sum over a one-dimensional block in a fixed order; valid in thread 0.
+// `sh` holds at least blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_allsum(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) t += sh[w];
+    return t;
 }
 
 }  // namespace cola

@@ -578,6 +578,12 @@ static bool tuning_enabled() {
     return on;
 }
 
+// While a TuneOnlyScope is alive on this thread, launch_dslash tunes unseen
+// configurations and launches nothing else.
+static thread_local int g_tune_only = 0;
+TuneOnlyScope::TuneOnlyScope() { ++g_tune_only; }
+TuneOnlyScope::~TuneOnlyScope() { --g_tune_only; }
+
 static bool outputs_alias_inputs(const DslashArgs &A) {
     for (int l = 0; l < A.nlat; ++l)
         if (A.lat[l].out == A.lat[l].in || A.lat[l].out == A.lat[l].xin) return true;
@@ -647,6 +653,7 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
             }
         }
     }
+    if (g_tune_only) return cudaSuccess;
     if (prec != COLA_F64 && staged_depth(prec) > 0 && block_x * A.rhs_per_block != kStagedThreads) {
         // the staged kernel's shared-memory layout is built for kStagedThreads threads
         A.rhs_per_block = std::min(A.rhs_per_block, 4);

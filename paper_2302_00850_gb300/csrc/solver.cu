@@ -57,7 +57,7 @@ namespace {
 enum Slot {
     S_T = 0, S_MP = 1,              // low-precision temporaries of the operator
     S_P = 2, S_Q = 3, S_RLO = 4, S_XLO = 5,
-    S_B = 6, S_XHI = 7, S_RHI = 8, S_AX = 9, S_T64 = 10, S_MP64 = 11, S_BORIG = 12, S_NORMS = 13,
+    S_B = 6, S_XHI = 7, S_RHI = 8, S_AX = 9, S_T64 = 10, S_MP64 = 11, S_BORIG = 12, S_NORMS = 13, S_FLAGS = 14,
 };
 
 // Vectors of one lattice of the batch (full packed fields x nrhs, held in
@@ -113,9 +113,7 @@ BlasArgs blas(const SolveCtx &c, std::initializer_list<std::pair<VecId, int>> id
     }
     B.state = c.owner->states;
     B.partials = c.owner->partials;
-    B.pstride = red_pstride(blas_max_warps(B));
-    B.counters = c.owner->counters;
-    B.cstride = red_cstride(blas_max_warps(B));
+    B.pstride = blas_max_blocks(B);
     return B;
 }
 
@@ -342,11 +340,9 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         COLA_TRY(ws_slot(g, S_MP64, hi, &L.mp64));
         L.borig = nullptr;
         if (dirac) COLA_TRY(ws_slot(g, S_BORIG, hi, &L.borig));
-        const int blas_warps = (G.Vh * 2 + 255) / 256 * 8;
-        const int ds_warps = ((G.Vh + 31) / 32 + 8) * 2;  // any tuned block shape
-        maxblocks = std::max(maxblocks, std::max(blas_warps, ds_warps));
+        maxblocks = std::max(maxblocks, (G.Vh * 2 + 255) / 256);  // vector kernels: 256 sites per block
     }
-    COLA_TRY(ws_reduce(c.owner, nrows, red_pstride(maxblocks), (size_t)nrows * red_cstride(maxblocks)));
+    COLA_TRY(ws_reduce(c.owner, nrows, maxblocks));
     COLA_TRY(ws_states(c.owner, nrows));
     CgState *hs = c.owner->h_states;
 
@@ -391,8 +387,29 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         BlasArgs B = blas(c, {{V_B, COLA_F64}});
         COLA_CUDA(launch_init_norms(B, s), "|b|^2");
     }
-    // r = b - A x0 in FP64, r_lo = p = r
-    COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, s));
+    // r = b - A x0 in FP64, r_lo = p = r.  A cold start (x0 all zero, the
+    // usual case) skips the FP64 operator: A x0 = 0.
+    {
+        unsigned *d_flags;
+        COLA_TRY(ws_slot(c.owner, S_FLAGS, nrows * sizeof(unsigned), reinterpret_cast<void **>(&d_flags)));
+        COLA_CUDA(cudaMemsetAsync(d_flags, 0, nrows * sizeof(unsigned), s), "zero flags");
+        BlasArgs B = blas(c, {{V_XHI, COLA_F64}});
+        COLA_CUDA(launch_any_nonzero(B, d_flags, s), "x0 check");
+        std::vector<unsigned> h(nrows);
+        COLA_CUDA(cudaMemcpyAsync(h.data(), d_flags, nrows * sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                  "x0 check readback");
+        COLA_CUDA(cudaStreamSynchronize(s), "x0 check");
+        bool any = false;
+        for (unsigned f : h) any |= f != 0;
+        if (any) {
+            COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, s));
+        } else {
+            for (int l = 0; l < nlat; ++l)
+                COLA_CUDA(cudaMemsetAsync(c.lat[l].ax, 0, 2 * spinor_parity_bytes(COLA_F64, c.lat[l].g->geom.Vh) * c.nrhs,
+                                          s),
+                          "zero A x0");
+        }
+    }
     {
         BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
         B.init = 1;
@@ -411,9 +428,11 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
     }
     if (running && prm->use_graph) {
         // Kernels launched while a stream is capturing are not autotuned, so
-        // tune the inner operator once here: q = A p is recomputed by the
-        // first iteration before anything reads it.
+        // tune the inner and the FP64 operators here (only configurations not
+        // seen before run, into buffers that are rewritten before use).
+        TuneOnlyScope tune_only;
         COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, nullptr, false, s));
+        COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, nullptr, false, s));
     }
     if (running) COLA_TRY(prm->use_graph ? run_graph_loop(c, s) : run_host_loop(c, s));
     {
