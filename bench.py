@@ -396,6 +396,19 @@ def multi_rhs_measurements(cola, dev):
         bs.append(torch.from_numpy(synth.gaussian_spinor(d, synth.seed_for(3, 8 + k), nrhs=4)).to(dev))
     msb, (xb, ib) = timed(lambda: cola.cg_solve_batched(gauges, bs, tol=TOL, op="eo", inner="f32", delta=DELTA,
                                                          use_graph=True))
+    # (c) the HMC force: phi = D^dag eta on 24^3x48 (links exp(0.3 i H), kappa 0.124),
+    #     X = (D^dag D)^-1 phi by FP32-inner CG on the whole lattice, Y = D X, force
+    u4 = synth.gauge_field(d24, 0.3, synth.seed_for(4, 0), device=dev, as_numpy=False)
+    g4 = cola.Gauge(u4, d24, kappa, BC, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
+    eta = torch.from_numpy(synth.gaussian_spinor(d24, synth.seed_for(4, 1))).to(dev)
+    phi = cola.apply_dirac(g4, eta, dagger=True)
+    msx, (X, ix) = timed(lambda: cola.cg_solve(g4, phi, tol=TOL, op="full", inner="f32", delta=DELTA,
+                                               use_graph=True))
+    Y = cola.apply_dirac(g4, X)
+    msf, F = timed(lambda: cola.fermion_force(g4, X, Y))
+    out["force_24x24x24x48"] = {"solve_ms": msx, "iters": ix[0].iters, "true_rel_resid": ix[0].true_rel_resid,
+                                "force_kernel_ms": msf, "links": 4 * 24 ** 3 * 48}
+    del g4, u4
     out["batched_4_lattices_x4"] = {
         "lattices": ["8^4", "12^3x24", "16^3x32", "24^3x48"], "nrhs": 4, "ms": msb,
         "max_iters": max(i.iters for row in ib for i in row),
