@@ -150,39 +150,120 @@ __device__ __forceinline__ void boundary_phase(const Geom &g, int mu, bool conj_
     else phase_mul(w, pr, pi);
 }
 
+// Rows 0 and 1 of acc += sc * c (no reconstruction: c is a sum of hops).
+template <typename R>
+__device__ __forceinline__ void accumulate01(Cx<R> (&acc)[12], const Cx<R> (&c)[2][3], R sc) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a].re = fma(sc, c[0][a].re, acc[a].re);
+        acc[a].im = fma(sc, c[0][a].im, acc[a].im);
+        acc[3 + a].re = fma(sc, c[1][a].re, acc[3 + a].re);
+        acc[3 + a].im = fma(sc, c[1][a].im, acc[3 + a].im);
+    }
+}
+
+// Rows 2 and 3 of the reconstruction of d with projector sign S, times sc.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate23(Cx<R> (&acc)[12], const Cx<R> (&d)[2][3], R sc) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (MU == 0) {
+            acc[6 + a].re = fma(S * sc, d[1][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, d[1][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, d[0][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, d[0][a].re, acc[9 + a].im);
+        } else if constexpr (MU == 1) {
+            acc[6 + a].re = fma(S * sc, d[1][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, d[1][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, d[0][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, d[0][a].im, acc[9 + a].im);
+        } else if constexpr (MU == 2) {
+            acc[6 + a].re = fma(S * sc, d[0][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, d[0][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, d[1][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, d[1][a].re, acc[9 + a].im);
+        } else {
+            acc[6 + a].re = fma(S * sc, d[0][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, d[0][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, d[1][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, d[1][a].im, acc[9 + a].im);
+        }
+    }
+}
+
+// c += U^dag h (continues the multiply-add chains that produced c).
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul_add(const Cx<R> (&u)[9], const Cx<R> (&h)[2][3], Cx<R> (&c)[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cmac_conj(c[k][a], u[a], h[k][0]);
+            cmac_conj(c[k][a], u[3 + a], h[k][1]);
+            cmac_conj(c[k][a], u[6 + a], h[k][2]);
+        }
+}
+
+// Both hops of direction mu, results scaled by bs (the output factor b).
+// The forward and backward reconstructions differ only in the sign of their
+// lower two rows, so away from the boundary both hops enter as
+//   rows 0,1 += bs (w_f + w_b),   rows 2,3 += bs C_f (w_f - w_b),
+// with c = w_f + w_b built by continuing w_f's multiply-add chains and
+// w_f - w_b = 2 w_f - c: twelve multiply-adds fewer than two full
+// reconstructions.  Hops that cross the boundary (phase) or carry an FP16
+// site scale take the general form.
 template <int P, int RECON, int MU, bool DAGGER>
 __device__ __forceinline__ void hop_mu(const DslashLat &A, const Coord &c, int cb, const char *in,
                                        const char *links_out, const char *links_in,
-                                       Cx<typename Prec<P>::real> (&acc)[12]) {
+                                       Cx<typename Prec<P>::real> (&acc)[12], typename Prec<P>::real bs) {
     using R = typename Prec<P>::real;
     const Geom &g = A.g;
     constexpr int SF = DAGGER ? +1 : -1;  // forward projector 1 + SF gamma
     constexpr int SB = -SF;
+    const int nbf = nbr_cb<MU, +1>(g, c, cb);
+    const int nbb = nbr_cb<MU, -1>(g, c, cb);
+    Cx<R> hf[2][3], hb[2][3], uf[9], ub[9];
+    R scf, scb;
     {
-        const int nb = nbr_cb<MU, +1>(g, c, cb);
         Cx<R> psi[12];
-        R sc = SpinorIO<P>::load_raw(in, g.Vh, nb, psi);
-        Cx<R> h[2][3];
-        project<MU, SF>(psi, h);
-        Cx<R> u[9];
-        LinkIO<P, RECON>::load(links_out + MU * A.link_dir_stride, g.Vh, cb, u);
-        Cx<R> w[2][3];
-        su3_mul(u, h, w);
-        if (!g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1) boundary_phase(g, MU, false, w, sc);
-        accumulate<MU, SF>(acc, w, sc);
+        scf = SpinorIO<P>::load_raw(in, g.Vh, nbf, psi);
+        project<MU, SF>(psi, hf);
     }
+    LinkIO<P, RECON>::load(links_out + MU * A.link_dir_stride, g.Vh, cb, uf);
     {
-        const int nb = nbr_cb<MU, -1>(g, c, cb);
         Cx<R> psi[12];
-        R sc = SpinorIO<P>::load_raw(in, g.Vh, nb, psi);
-        Cx<R> h[2][3];
-        project<MU, SB>(psi, h);
-        Cx<R> u[9];
-        LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nb, u);
-        Cx<R> w[2][3];
-        su3_adj_mul(u, h, w);
-        if (!g.bc_trivial[MU] && coord_of<MU>(c) == 0) boundary_phase(g, MU, true, w, sc);
-        accumulate<MU, SB>(acc, w, sc);
+        scb = SpinorIO<P>::load_raw(in, g.Vh, nbb, psi);
+        project<MU, SB>(psi, hb);
+    }
+    LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nbb, ub);
+    const bool edge_f = !g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1;
+    const bool edge_b = !g.bc_trivial[MU] && coord_of<MU>(c) == 0;
+    Cx<R> wf[2][3];
+    su3_mul(uf, hf, wf);
+    if (P != COLA_F16 && !edge_f && !edge_b) {
+        Cx<R> cs[2][3];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cs[k][a] = wf[k][a];
+        su3_adj_mul_add(ub, hb, cs);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                wf[k][a].re = fma(R(2), wf[k][a].re, -cs[k][a].re);
+                wf[k][a].im = fma(R(2), wf[k][a].im, -cs[k][a].im);
+            }
+        accumulate01(acc, cs, bs);
+        accumulate23<MU, SF>(acc, wf, bs);
+    } else {
+        R sf = scf * bs, sb = scb * bs;
+        if (edge_f) boundary_phase(g, MU, false, wf, sf);
+        accumulate<MU, SF>(acc, wf, sf);
+        Cx<R> wb[2][3];
+        su3_adj_mul(ub, hb, wb);
+        if (edge_b) boundary_phase(g, MU, true, wb, sb);
+        accumulate<MU, SB>(acc, wb, sb);
     }
 }
 
@@ -276,14 +357,14 @@ __device__ __forceinline__ void stage_issue(const DslashLat &A, const Coord &c, 
 
 template <int P, int RECON, int J, bool DAGGER>
 __device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c, const Stage<P, RECON> &st,
-                                              int tid, Cx<float> (&acc)[12]) {
+                                              int tid, Cx<float> (&acc)[12], float bs) {
     using L = HopLayout<P, RECON>;
     constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
     constexpr int SF = DAGGER ? +1 : -1;
     constexpr int S = DIR > 0 ? SF : -SF;
     const Geom &g = A.g;
     Cx<float> psi[12];
-    float sc = 1.0f;
+    float sc = bs;
     if constexpr (P == COLA_F16) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -294,7 +375,7 @@ __device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c
             psi[4 * k + 2] = {cc.x, cc.y};
             psi[4 * k + 3] = {d.x, d.y};
         }
-        sc = *st.scale(tid);
+        sc *= *st.scale(tid);
     } else {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -333,7 +414,7 @@ __device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c
 template <int P, int RECON, bool DAGGER, int NS, int J>
 __device__ __forceinline__ void staged_step(const DslashLat &A, const Coord &c, int cb, const char *in,
                                             const char *lo, const char *li, char *smem, int T, int tid,
-                                            Cx<float> (&acc)[12]) {
+                                            Cx<float> (&acc)[12], float bs) {
     using L = HopLayout<P, RECON>;
     if constexpr (J + NS - 1 < 8) {
         Stage<P, RECON> nx{smem + ((J + NS - 1) % NS) * L::bytes * kStagedThreads};
@@ -342,8 +423,8 @@ __device__ __forceinline__ void staged_step(const DslashLat &A, const Coord &c, 
     cp_async_commit();
     cp_async_wait<NS - 1>();
     Stage<P, RECON> cur{smem + (J % NS) * L::bytes * kStagedThreads};
-    stage_compute<P, RECON, J, DAGGER>(A, c, cur, tid, acc);
-    if constexpr (J < 7) staged_step<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid, acc);
+    stage_compute<P, RECON, J, DAGGER>(A, c, cur, tid, acc, bs);
+    if constexpr (J < 7) staged_step<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid, acc, bs);
 }
 
 template <int P, int RECON, bool DAGGER, int NS, int J>
@@ -360,12 +441,12 @@ __device__ __forceinline__ void staged_prologue(const DslashLat &A, const Coord 
 
 template <int P, int RECON, bool DAGGER, int NS>
 __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, int cb, const char *in,
-                                            const char *lo, const char *li, Cx<float> (&acc)[12]) {
+                                            const char *lo, const char *li, Cx<float> (&acc)[12], float bs) {
     extern __shared__ __align__(16) char smem_dyn[];
     constexpr int T = kStagedThreads;  // blockDim.x * blockDim.y, enforced by launch_dslash
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     staged_prologue<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid);
-    staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc);
+    staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc, bs);
 }
 
 // Grid: x over the site blocks of every lattice of the batch (lattice l owns
@@ -405,14 +486,14 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) dslash_kernel(const 
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
         if constexpr (NS > 0 && P != COLA_F64) {
-            hops_staged<P, RECON, DAGGER, NS>(L, c, cb, in, lo, li, acc);
+            hops_staged<P, RECON, DAGGER, NS>(L, c, cb, in, lo, li, acc, (float)L.b);
         } else {
-            hop_mu<P, RECON, 0, DAGGER>(L, c, cb, in, lo, li, acc);
-            hop_mu<P, RECON, 1, DAGGER>(L, c, cb, in, lo, li, acc);
-            hop_mu<P, RECON, 2, DAGGER>(L, c, cb, in, lo, li, acc);
-            hop_mu<P, RECON, 3, DAGGER>(L, c, cb, in, lo, li, acc);
+            hop_mu<P, RECON, 0, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 1, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 2, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 3, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
         }
-        const R b = (R)L.b;
+        // the factor b is already in every hop's scale
         if constexpr (XPAY) {
             const R a = (R)L.a;
             Cx<R> xs[12];
@@ -420,14 +501,8 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) dslash_kernel(const 
                               g.Vh, cb, xs);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                acc[k].re = a * xs[k].re + b * acc[k].re;
-                acc[k].im = a * xs[k].im + b * acc[k].im;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                acc[k].re *= b;
-                acc[k].im *= b;
+                acc[k].re = fma(a, xs[k].re, acc[k].re);
+                acc[k].im = fma(a, xs[k].im, acc[k].im);
             }
         }
     }
