@@ -449,9 +449,11 @@ __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, 
     staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc, bs);
 }
 
-// Grid: x over the site blocks of every lattice of the batch (lattice l owns
-// blocks [block0, block0 + nblocks)), y over right-hand-side groups, z over
-// the output parities (1 or 2).  Block: (sites, right-hand sides).
+// Grid: x over (site block, right-hand-side group) pairs of every lattice of
+// the batch, group fastest (lattice l owns [block0, block0 + nblocks *
+// ngroups)), so that the blocks reading the same links run back to back and
+// find them in L1/L2; z over the output parities (1 or 2).
+// Block: (sites, right-hand sides).
 // Register budget: FP16/FP32 at two 256-thread blocks per SM (128 registers,
 // no spills); FP64 is bound by the FP64 pipe and keeps its full register set.
 template <int P>
@@ -466,8 +468,11 @@ __global__ void __launch_bounds__(256, MinBlocks<P>::value) dslash_kernel(const 
     while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
     const DslashLat &L = A.lat[l];
     const Geom &g = L.g;
-    const int cb = ((int)blockIdx.x - L.block0) * blockDim.x + threadIdx.x;
-    const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
+    const int rel = (int)blockIdx.x - L.block0;
+    const int grp = A.ngroups == 1 ? 0 : rel % A.ngroups;
+    const int sblk = A.ngroups == 1 ? rel : rel / A.ngroups;
+    const int cb = sblk * blockDim.x + threadIdx.x;
+    const int rhs = grp * blockDim.y + threadIdx.y;
     const int row = L.row0 + rhs;
     const int par = A.parity0 + blockIdx.z;
     const bool row_ok = rhs < A.nrhs;
@@ -527,7 +532,7 @@ template <int P, int RECON, bool DAGGER, bool XPAY, int NS>
 static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total_blocks, cudaStream_t s) {
     const int by = A.rhs_per_block;
     dim3 block(bx, by, 1);
-    dim3 grid(total_blocks, (A.nrhs + by - 1) / by, nparity);
+    dim3 grid(total_blocks, 1, nparity);
     size_t smem = 0;
     if constexpr (NS > 0 && P != COLA_F64) {
         smem = (size_t)NS * HopLayout<P, RECON>::bytes * bx * by;
@@ -561,21 +566,22 @@ static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, bool 
                 : launch_t<P, RECON, false, false>(A, nparity, bx, nb, s);
 }
 
-// Site blocks per lattice for block_x; returns the total.
+// Site blocks per lattice for block_x (each repeated for the ngroups
+// right-hand-side groups); returns the grid size.
 static int assign_blocks(DslashArgs &A, int bx) {
     int total = 0;
     for (int l = 0; l < A.nlat; ++l) {
         A.lat[l].block0 = total;
         A.lat[l].nblocks = (A.lat[l].g.Vh + bx - 1) / bx;
-        total += A.lat[l].nblocks;
+        total += A.lat[l].nblocks * A.ngroups;
     }
     return total;
 }
 
 static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
                               cudaStream_t s) {
-    const int nb = assign_blocks(A, block_x);
     A.ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
+    const int nb = assign_blocks(A, block_x);
     switch (prec) {
         case COLA_F64:
             return recon == 12 ? launch_r<COLA_F64, 12>(A, nparity, dagger, xpay, block_x, nb, s)
