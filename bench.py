@@ -43,6 +43,7 @@ METRIC = "Wilson Dslash GFLOP/s & HBM GB/s; mixed-vs-FP64 CG time at 1e-10 resid
 # algorithmic bytes per output site of one parity apply (FP16 storage, 12-real links):
 # 8 links x 24 B + input spinor 48 B + its FP32 scale + output 48 B + scale
 BYTES_PER_SITE_F16 = 8 * 24 + 52 + 52
+BYTES_PER_SITE_F32 = 8 * 48 + 96 + 96
 # FP64 peak of this part from its unit counts and clock: 152 SMs x 2 DFMA per
 # SM per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2 flop
 # x 2.07 GHz maximum SM clock.
@@ -278,29 +279,67 @@ def run_cola(args):
     torch.cuda.synchronize()
     ds64_us = d0.elapsed_time(d1) * 1e3 / 20
 
+    # isolated FP32 parity Dslash (the FP32-storage solver's kernel), own handle
+    g32 = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f32",), recon={"f32": 12})
+    p32 = cola.pack(g32, b, "f32")
+    t32 = g32.empty_packed("f32")
+    for _ in range(3):
+        cola.dslash(g32, t32, p32, parity=1, prec="f32")
+        cola.dslash(g32, p32, t32, parity=0, prec="f32")
+    torch.cuda.synchronize()
+    d0.record(stream)
+    for _ in range(50):
+        cola.dslash(g32, t32, p32, parity=1, prec="f32")
+        cola.dslash(g32, p32, t32, parity=0, prec="f32")
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ds32_us = d0.elapsed_time(d1) * 1e3 / 100
+    ds32_gbs = BYTES_PER_SITE_F32 * vh / (ds32_us * 1e-6) / 1e9
+    del g32, p32, t32
+
     multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
 
     # end to end through the public API with host buffers: every step copies
     # the canonical links and the source from pinned host memory, re-packs the
-    # links into the (reused) gauge handle, solves and copies x back
+    # links into the (reused) gauge handle, solves and copies x back.  Copies
+    # run on their own stream, double-buffered, so step k+1's inputs and step
+    # k-1's result move while step k solves; all of them are inside the timed
+    # region.
     u_host = u.cpu().pin_memory()
     b_host = b.cpu().pin_memory()
-    x_host = torch.empty_like(b_host).pin_memory()
-    ud = torch.empty_like(u)
-    bd = torch.empty_like(b)
+    e2e_steps = max(2, min(args.steps, 4))
+    x_host = [torch.empty_like(b_host).pin_memory() for _ in range(2)]
+    ud = [torch.empty_like(u) for _ in range(2)]
+    bd = [torch.empty_like(b) for _ in range(2)]
+    copy = torch.cuda.Stream(device=dev)
+    main = torch.cuda.current_stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    keep = []
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
     w0 = time.perf_counter()
+    with torch.cuda.stream(copy):
+        ud[0].copy_(u_host, non_blocking=True)
+        bd[0].copy_(b_host, non_blocking=True)
+        ev_in[0].record(copy)
     e2e_ds = 0
-    for _ in range(e2e_steps):
-        ud.copy_(u_host, non_blocking=True)
-        bd.copy_(b_host, non_blocking=True)
-        g.update(ud)
-        xe, ie = cola.cg_solve(g, bd, tol=TOL, op="eo", inner="f16", delta=DELTA, use_graph=True)
-        x_host.copy_(xe, non_blocking=True)
-        torch.cuda.synchronize()
+    for k in range(e2e_steps):
+        cur, nxt = k % 2, (k + 1) % 2
+        if k + 1 < e2e_steps:
+            with torch.cuda.stream(copy):
+                ud[nxt].copy_(u_host, non_blocking=True)
+                bd[nxt].copy_(b_host, non_blocking=True)
+                ev_in[nxt].record(copy)
+        main.wait_event(ev_in[cur])
+        g.update(ud[cur])
+        xe, ie = cola.cg_solve(g, bd[cur], tol=TOL, op="eo", inner="f16", delta=DELTA, use_graph=True)
         e2e_ds += 4 * ie[0].iters + 4 * ie[0].reliable_updates
+        copy.wait_stream(main)
+        with torch.cuda.stream(copy):
+            x_host[cur].copy_(xe, non_blocking=True)
+        keep.append(xe)
+    torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - w0) / e2e_steps
+    del keep
     e2e_value = FLOP_PER_SITE * vh * (e2e_ds / e2e_steps) * world / e2e_s / 1e9
 
     cpu = None
@@ -323,6 +362,8 @@ def run_cola(args):
             "dslash_f16": {"us_per_parity_apply": ds_us, "gflops": FLOP_PER_SITE * vh / (ds_us * 1e-6) / 1e9,
                            "algorithmic_gbs": achieved},
             "dslash_f64": {"us_per_parity_apply": ds64_us, "gflops": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e9},
+            "dslash_f32": {"us_per_parity_apply": ds32_us, "gflops": FLOP_PER_SITE * vh / (ds32_us * 1e-6) / 1e9,
+                           "algorithmic_gbs": ds32_gbs, "hbm_frac": ds32_gbs / peak},
             # dominant kernel by time share: the FP64 hopping term of the reliable
             # updates (about half of the solve), bound by the FP64 pipe
             "roofline": {"bound": "alu", "achieved": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12,
@@ -338,7 +379,8 @@ def run_cola(args):
                                "peak_kind": f"{peak_kind} hbm_gbs (burst, kernel timed alone)"},
             "e2e": {"value": e2e_value, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": u_host.numel() * 16 + b_host.numel() * 16,
-                    "d2h_bytes_per_step": x_host.numel() * 16, "ms_per_step": e2e_s * 1e3},
+                    "d2h_bytes_per_step": x_host[0].numel() * 16, "ms_per_step": e2e_s * 1e3,
+                    "overlap": "copies double-buffered on a copy stream, overlapping the previous and next solve"},
             "multi_rhs": multi,
             "gpu_launches": launches,
             "clocks": clocks,

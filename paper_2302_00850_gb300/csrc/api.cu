@@ -269,6 +269,7 @@ cola_status cola_gauge_destroy(cola_gauge g) {
     if (g->partials) cudaFree(g->partials);
     if (g->states) cudaFree(g->states);
     if (g->h_states) cudaFreeHost(g->h_states);
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
     delete g;
     return COLA_OK;
 }

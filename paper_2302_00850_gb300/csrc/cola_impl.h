@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "cola_internal.cuh"
 
@@ -134,6 +135,10 @@ struct cola_gauge_s {
     cola::CgState *states = nullptr;   // device
     cola::CgState *h_states = nullptr; // pinned host mirror
     int states_count = 0;
+    // the instantiated solve graph of the last graph-driven solve this handle
+    // led, and the bytes of the configuration it was captured for
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<unsigned char> graph_key;
 };
 
 namespace cola {

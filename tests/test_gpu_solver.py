@@ -196,3 +196,28 @@ def test_eo_solve_16x16x16x32_workload(cola, inner):
     assert info[0].status == 0
     r = true_resid_eo(u, x.cpu().numpy(), b, kappa, dims)
     assert r <= 1e-10 and abs(r - info[0].true_rel_resid) < 1e-12
+
+
+def test_cached_solve_graph_is_reused_and_stays_correct(cola):
+    """A second graph-driven solve of the same configuration launches the cached graph."""
+    dims = (8, 8, 8, 16)
+    kappa = 0.125
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(1, 0))
+    g = cola.Gauge(to_dev(u), dims, kappa, BC_AP, precisions=("f64", "f16"))
+    b1 = synth.gaussian_spinor(dims, synth.seed_for(1, 1))
+    b2 = synth.gaussian_spinor(dims, synth.seed_for(1, 2))
+    xa, ia = cola.cg_solve(g, to_dev(b1), op="eo", inner="f16", use_graph=True)
+    xb, ib = cola.cg_solve(g, to_dev(b2), op="eo", inner="f16", use_graph=True)   # cached graph, new source
+    xc, ic = cola.cg_solve(g, to_dev(b1), op="eo", inner="f16", use_graph=True)   # cached graph again
+    assert bool((xa == xc).all()) and ia[0].iters == ic[0].iters
+    assert true_resid_eo(u, xb.cpu().numpy(), b2, kappa, dims) <= 1e-10
+    # new links in the same handle: the cached graph reads the re-packed links
+    u2 = synth.gauge_field(dims, 0.3, synth.seed_for(1, 5))
+    g.update(to_dev(u2))
+    xd, idd = cola.cg_solve(g, to_dev(b1), op="eo", inner="f16", use_graph=True)
+    assert true_resid_eo(u2, xd.cpu().numpy(), b1, kappa, dims) <= 1e-10
+    # a different number of right-hand sides rebuilds the graph
+    b3 = synth.gaussian_spinor(dims, synth.seed_for(1, 3), nrhs=2)
+    x3, i3 = cola.cg_solve(g, to_dev(b3), op="eo", inner="f16", use_graph=True)
+    for r in range(2):
+        assert true_resid_eo(u2, x3[r].cpu().numpy(), b3[r], kappa, dims) <= 1e-10
