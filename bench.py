@@ -58,6 +58,26 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate_ranks(t_ms, units, device=None):
+    """Whole-job timing over the ranks of a replicas run: (max time, summed units).
+
+    Every rank solves its own copy of the workload (no data-path collective);
+    only these two scalars cross ranks.  Without an initialised process group
+    this is the identity.
+    """
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_ms), float(units)
+    dev = device if device is not None else torch.device("cpu")
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons while running."""
 
@@ -217,17 +237,11 @@ def run_cola(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-
     iters = [i.iters for i in infos]
     rus = [i.reliable_updates for i in infos]
     # parity Dslash applies per solve: 4 per iteration (inner precision) + 4 per FP64 residual
     n_ds = [4 * it + 4 * ru for it, ru in zip(iters, rus)]
-    flops = sum(FLOP_PER_SITE * vh * n for n in n_ds) * world
+    t_ms, flops = aggregate_ranks(ev0.elapsed_time(ev1), sum(FLOP_PER_SITE * vh * n for n in n_ds), dev)
     value = flops / (t_ms * 1e-3) / 1e9
     # kernels per solve: 9 set-up/finish launches (packing, |b|^2 and its
     # finishing kernel, the zero-guess check, initial residual and finisher,
@@ -340,7 +354,9 @@ def run_cola(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - w0) / e2e_steps
     del keep
-    e2e_value = FLOP_PER_SITE * vh * (e2e_ds / e2e_steps) * world / e2e_s / 1e9
+    e2e_ms, e2e_flops = aggregate_ranks(e2e_s * 1e3, FLOP_PER_SITE * vh * e2e_ds / e2e_steps, dev)
+    e2e_s = e2e_ms * 1e-3
+    e2e_value = e2e_flops / e2e_s / 1e9
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -456,13 +456,19 @@ __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, 
 // Block: (sites, right-hand sides).
 // Register budget: FP16/FP32 at two 256-thread blocks per SM (128 registers,
 // no spills); FP64 is bound by the FP64 pipe and keeps its full register set.
-template <int P>
-struct MinBlocks {
-    static constexpr int value = P == COLA_F64 ? 1 : COLA_DSLASH_MINB;
+// The staged kernels always run 128-thread blocks.
+#ifndef COLA_STAGED_MINB
+#define COLA_STAGED_MINB 5
+#endif
+template <int P, int NS>
+struct LaunchShape {
+    static constexpr int threads = NS > 0 ? 128 : 256;
+    static constexpr int min_blocks = P == COLA_F64 ? 1 : NS > 0 ? COLA_STAGED_MINB : COLA_DSLASH_MINB;
 };
 
 template <int P, int RECON, bool DAGGER, bool XPAY, int NS>
-__global__ void __launch_bounds__(256, MinBlocks<P>::value) dslash_kernel(const __grid_constant__ DslashArgs A) {
+__global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS>::min_blocks)
+    dslash_kernel(const __grid_constant__ DslashArgs A) {
     using R = typename Prec<P>::real;
     int l = 0;
     while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
