@@ -102,3 +102,21 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.cola_cg_solve(None, None, None, None, None, None) == -1
     assert lib.cola_dslash_apply(None, None, None, None, 0.0, 1.0, 0, 0, 0, 1, None) == -1
     assert lib.cola_gauge_destroy(None) == 0
+
+
+def test_solver_parameter_errors_before_any_cuda_call(lib):
+    from paper_2302_00850_gb300 import _lib
+
+    fake = ctypes.c_void_p(1)  # never dereferenced: parameters are checked first
+    info = (_lib.SolveInfo * 1)()
+    for kw in [dict(nrhs=0), dict(nrhs=65), dict(tol=0.0), dict(max_iter=-1), dict(op=7), dict(system=3),
+               dict(inner=5), dict(inner=2, delta=1.5)]:
+        p = dict(tol=1e-10, max_iter=10, op=1, system=0, inner=0, delta=0.1, nrhs=1, use_graph=0)
+        p.update(kw)
+        prm = _lib.SolverParams(p["tol"], p["max_iter"], p["op"], p["system"], p["inner"], p["delta"], p["nrhs"],
+                                p["use_graph"])
+        assert lib.cola_cg_solve(fake, fake, fake, ctypes.byref(prm), info, None) == -1, kw
+    hs = (ctypes.c_void_p * 1)(1)
+    prm = _lib.SolverParams(1e-10, 10, 1, 0, 0, 0.1, 1, 0)
+    assert lib.cola_cg_solve_batched(0, hs, hs, hs, ctypes.byref(prm), info, None) == -1
+    assert lib.cola_cg_solve_batched(9, hs, hs, hs, ctypes.byref(prm), info, None) == -1
