@@ -95,3 +95,48 @@ def test_force_24x24x24x48_sampled_links(cola):
     assert rel_err(got, want) < 1e-13
     # Y = D X and the phi = D^dag eta structure: X is the solution of D^dag D X = D^dag eta, so D X = eta
     assert rel_err(Yn, eta) < 1e-8
+
+
+def _eo_resid(u, x, b, kappa, dims):
+    e = oracle.even_mask(dims)[..., None, None]
+    return rel_err(oracle.mdagm_eo(u, x * e, kappa, BC_AP) * e, b * e)
+
+
+def test_point_sources_and_batch_full_size(cola):
+    """12 point sources on 24^3x48 in one graph-captured FP32/FP64 solve, then the batch
+    8^4 + 12^3x24 + 16^3x32 + 24^3x48 with 4 Gaussian sources each; residuals by the oracle."""
+    import torch
+
+    kappa = 0.124
+    d24 = (24, 24, 24, 48)
+    u24d = synth.gauge_field(d24, 0.3, synth.seed_for(3, 0), device="cuda", as_numpy=False)
+    g24 = cola.Gauge(u24d, d24, kappa, BC_AP, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
+    pts = synth.point_sources(d24)
+    x, infos = cola.cg_solve(g24, to_dev(pts), tol=1e-10, op="eo", inner="f32", delta=0.1, use_graph=True)
+    assert all(i.status == 0 for i in infos)
+    u24 = u24d.cpu().numpy()
+    xs = x.cpu().numpy()
+    del x
+    for r in (0, 7, 11):
+        assert _eo_resid(u24, xs[r], pts[r], kappa, d24) <= 1e-10
+    del xs
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), d24]
+    gauges, bs, us = [], [], []
+    for k, d in enumerate(dims_list):
+        if d == d24:
+            u, g = u24, g24
+        else:
+            u = synth.gauge_field(d, 0.3, synth.seed_for(3, 4 + k))
+            g = cola.Gauge(to_dev(u), d, kappa, BC_AP, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
+        us.append(u)
+        gauges.append(g)
+        bs.append(synth.gaussian_spinor(d, synth.seed_for(3, 8 + k), nrhs=4))
+    xb, ib = cola.cg_solve_batched(gauges, [to_dev(b) for b in bs], tol=1e-10, op="eo", inner="f32", delta=0.1,
+                                   use_graph=True)
+    for k, d in enumerate(dims_list):
+        assert all(i.status == 0 for i in ib[k])
+        rows = range(4) if d != d24 else (2,)
+        xk = xb[k].cpu().numpy()
+        for r in rows:
+            assert _eo_resid(us[k], xk[r], bs[k][r], kappa, d) <= 1e-10
+    torch.cuda.empty_cache()
