@@ -18,6 +18,8 @@ definitions, each stated where it is coded:
   solve.py   Hestenes-Stiefel CG with true-residual confirmation, the
              even-odd normal-equation solve, dense matrices for brute force
   force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
+  clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H
+             and its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe
 
 Pins (tests/test_oracle_*.py, run without a GPU): gamma algebra; the free
 field closed form (plane waves and the full D^dag D spectrum); gamma5
@@ -25,7 +27,11 @@ hermiticity and the adjoint identity; gauge covariance under random SU(3)
 transformations; brute-force dense solves on 2^4; the Schur identity between
 the even-odd and full solves; the force against central finite differences of
 an exactly computed action and against the closed form S = |eta|^2 at
-phi = D^dag eta.  Every function here is pinned by at least one of them.
+phi = D^dag eta; for the clover term the unit-gauge reduction, a constant
+abelian field in closed form, the weak-field lattice curl, gauge covariance,
+dense Schur identities and the tree-level cancellation of the Wilson lift of
+Landau zero modes (which fixes its sign).  Every function here is pinned by
+at least one of them.
 """
 from .wilson import (  # noqa: F401
     GAMMA, GAMMA5, IDENTITY4, parity_of_sites, even_mask, phased_links, hop,

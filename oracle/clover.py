@@ -1,0 +1,133 @@
+"""Clover (Sheikholeslami-Wohlert) term, FP64 (test infrastructure only).
+
+The paper's overview of COLA's physics features cites the clover-improved
+Wilson actions (FLIC fermions among them) that the library runs but writes no
+formula for them.  The definitions here are the standard Sheikholeslami-
+Wohlert term in the kappa normalisation of wilson.py (Luscher et al. 1996
+sign and clover-leaf field strength, with the traceless projection of F):
+
+  sigma_mn = (i/2) [gamma_m, gamma_n]                      (Hermitian)
+  Q_mn(x)  = sum of the four plaquettes in the (m, n) plane that touch x,
+             each oriented m -> n (the "clover" of leaves)
+  F_mn(x)  = (Q_mn - Q_mn^dag) / (8 i), minus its trace / 3  (Hermitian, traceless)
+  A(x)     = 1 - kappa c_sw sum_{m<n} sigma_mn F_mn(x)      (a 12x12 Hermitian matrix per site)
+  D_sw     = A - kappa H
+
+sigma_mn commutes with gamma5 = diag(1, 1, -1, -1), so A is block diagonal:
+one 6x6 block on spins (0, 1) and one on spins (2, 3).  The plaquettes use
+the gauge links without the fermion boundary phase (a closed loop carries
+the phase and its conjugate).
+
+Even-odd: D_sw = [[A_ee, -kappa H_eo], [-kappa H_oe, A_oo]], Schur operator on
+even sites Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe, det D_sw = det A_oo det Mhat,
+Mhat^dag = A_ee - kappa^2 H^dag_eo A_oo^-1 H^dag_oe = gamma5 Mhat gamma5.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .wilson import GAMMA, GAMMA5, hop, hop_block, parity_of_sites
+
+SIGMA = np.zeros((4, 4, 4, 4), dtype=np.complex128)
+for _m in range(4):
+    for _n in range(4):
+        SIGMA[_m, _n] = 0.5j * (GAMMA[_m] @ GAMMA[_n] - GAMMA[_n] @ GAMMA[_m])
+
+
+def _shift(f, mu, step):
+    """f(x + step * mu) for a field laid out [Lt, Lz, Ly, Lx, ...]."""
+    return np.roll(f, -step, axis=3 - mu)
+
+
+def _dag(m):
+    return np.conj(np.swapaxes(m, -1, -2))
+
+
+def _mm(*ms):
+    out = ms[0]
+    for m in ms[1:]:
+        out = np.einsum("...ab,...bc->...ac", out, m)
+    return out
+
+
+def clover_leaves(u, mu, nu):
+    """Q_mn(x): the four plaquettes of the (mu, nu) plane touching x, oriented mu -> nu."""
+    um, un = u[mu], u[nu]
+    p1 = _mm(um, _shift(un, mu, 1), _dag(_shift(um, nu, 1)), _dag(un))
+    p2 = _mm(un, _dag(_shift(_shift(um, mu, -1), nu, 1)), _dag(_shift(un, mu, -1)), _shift(um, mu, -1))
+    p3 = _mm(_dag(_shift(um, mu, -1)), _dag(_shift(_shift(un, mu, -1), nu, -1)), _shift(_shift(um, mu, -1), nu, -1),
+             _shift(un, nu, -1))
+    p4 = _mm(_dag(_shift(un, nu, -1)), _shift(um, nu, -1), _shift(_shift(un, mu, 1), nu, -1), _dag(um))
+    return p1 + p2 + p3 + p4
+
+
+def field_strength(u):
+    """F[(mu, nu)] for mu < nu: Hermitian traceless [Lt, Lz, Ly, Lx, 3, 3] arrays."""
+    out = {}
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            q = clover_leaves(u, mu, nu)
+            f = (q - _dag(q)) / 8j
+            tr = np.trace(f, axis1=-2, axis2=-1) / 3.0
+            out[(mu, nu)] = f - tr[..., None, None] * np.eye(3)
+    return out
+
+
+def clover_matrix(u, kappa, csw):
+    """A(x) as [Lt, Lz, Ly, Lx, 4, 3, 4, 3] (spin, colour; spin, colour)."""
+    f = field_strength(u)
+    lt, lz, ly, lx = u.shape[1:5]
+    a = np.zeros((lt, lz, ly, lx, 4, 3, 4, 3), dtype=np.complex128)
+    for s in range(4):
+        for c in range(3):
+            a[..., s, c, s, c] = 1.0
+    for (mu, nu), fmn in f.items():
+        a -= kappa * csw * np.einsum("st,...ab->...satb", SIGMA[mu, nu], fmn)
+    return a
+
+
+def apply_site_matrix(a, psi):
+    return np.einsum("...satb,...tb->...sa", a, psi)
+
+
+def invert_site_matrix(a):
+    shp = a.shape
+    m = a.reshape(shp[:4] + (12, 12))
+    return np.linalg.inv(m).reshape(shp)
+
+
+def dirac_clover(u, psi, kappa, bc, csw):
+    """D_sw psi = A psi - kappa H psi."""
+    return apply_site_matrix(clover_matrix(u, kappa, csw), psi) - kappa * hop(u, psi, bc)
+
+
+def dirac_clover_dag(u, psi, kappa, bc, csw):
+    """D_sw^dag psi = A psi - kappa H^dag psi (A is Hermitian)."""
+    return apply_site_matrix(clover_matrix(u, kappa, csw), psi) - kappa * hop(u, psi, bc, dagger=True)
+
+
+def mhat_clover(u, psi_e, kappa, bc, csw, dagger=False):
+    """Mhat psi_e = A_ee psi_e - kappa^2 H_eo A_oo^-1 H_oe psi_e (dagger: H -> H^dag)."""
+    dims = (psi_e.shape[3], psi_e.shape[2], psi_e.shape[1], psi_e.shape[0])
+    par = parity_of_sites(dims)
+    pe = psi_e * (par == 0)[..., None, None]
+    a = clover_matrix(u, kappa, csw)
+    ainv = invert_site_matrix(a)
+    t = hop_block(u, pe, bc, 1, dagger)
+    t = apply_site_matrix(ainv, t) * (par == 1)[..., None, None]
+    return (apply_site_matrix(a, pe) - kappa * kappa * hop_block(u, t, bc, 0, dagger)) * (par == 0)[..., None, None]
+
+
+def mdagm_eo_clover(u, psi_e, kappa, bc, csw):
+    return mhat_clover(u, mhat_clover(u, psi_e, kappa, bc, csw), kappa, bc, csw, dagger=True)
+
+
+def mdagm_full_clover(u, psi, kappa, bc, csw):
+    return dirac_clover_dag(u, dirac_clover(u, psi, kappa, bc, csw), kappa, bc, csw)
+
+
+def gamma5_commutator(a):
+    """Largest entry of |gamma5 A(x) - A(x) gamma5| over the lattice."""
+    g5a = np.einsum("su,...uatb->...satb", GAMMA5, a)
+    ag5 = np.einsum("...satb,tu->...saub", a, GAMMA5)
+    return float(np.max(np.abs(g5a - ag5)))
