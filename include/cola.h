@@ -111,9 +111,17 @@ cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const voi
                               double a, double b, int parity, int dagger, cola_prec prec,
                               int nrhs, cudaStream_t stream);
 
+/* out = D in (dagger: D^dag in) on packed fields, both parities, for each
+ * of nrhs right-hand sides: D = 1 - kappa H, or A - kappa H when the handle
+ * has a clover term.  out must not alias in. */
+cola_status cola_dirac_apply(cola_gauge g, void *out, const void *in, int dagger, cola_prec prec,
+                             int nrhs, cudaStream_t stream);
+
 /* out = M^dag M in on packed fields.  op COLA_OP_FULL: M = D on the whole
  * lattice.  op COLA_OP_EO: M = Mhat on the even half (the odd half of out is
- * left as it was).  Uses workspace held by the handle (allocated on first use). */
+ * left as it was).  With a clover term D = A - kappa H and
+ * Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe.  Uses workspace held by the
+ * handle (allocated on first use). */
 cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
                              int nrhs, cudaStream_t stream);
 
@@ -131,6 +139,38 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
  * streams, unordered threads) race, so order them. */
 cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
                                      int nrhs, cudaStream_t stream);
+
+/* Clover (Sheikholeslami-Wohlert) term.  The paper's list of COLA's physics
+ * features cites clover-improved Wilson actions (FLIC fermions among them)
+ * without writing them; this is the standard term in the kappa
+ * normalisation above:
+ *   A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_munu F_munu(x),
+ *   sigma_munu = (i/2)[gamma_mu, gamma_nu],
+ *   F_munu(x) = traceless part of (Q_munu(x) - Q_munu(x)^dag) / (8i),
+ * Q_munu(x) the sum of the four plaquettes of the (mu, nu) plane touching x,
+ * each oriented mu -> nu, from the links WITHOUT boundary phases.  Then
+ * D = A - kappa H and the even-odd Schur operator is
+ * Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe (det D = det A_oo det Mhat).
+ *
+ * cola_clover_attach builds A and A^-1 on every site from the handle's FP64
+ * links (the handle must hold COLA_F64) and stores both in each precision
+ * the handle holds (72 reals per site each; FP16 without a scale).  From then
+ * on cola_dirac_apply, cola_mdagm_apply(_noalloc) and cola_cg_solve(_batched)
+ * use the clover operator, cola_gauge_update rebuilds the term for the new
+ * links, and cola_fermion_force / cola_dirac_link_grad return
+ * COLA_ERR_UNSUPPORTED (they differentiate the hopping term only).
+ * cola_dslash_apply stays the bare hopping term.  csw = 0 removes the term.
+ * The call waits for its stream (it reads back a pivot flag): it returns
+ * COLA_ERR_BREAKDOWN, and leaves the handle without a clover term, if some
+ * A(x) block has a zero or non-finite pivot in its LDL^dag factorisation. */
+cola_status cola_clover_attach(cola_gauge g, double csw, cudaStream_t stream);
+/* c_sw of the attached clover term, 0 if none (or g is NULL). */
+double cola_clover_csw(cola_gauge g);
+/* out_p = A_pp in_p (inverse != 0: A_pp^-1 in_p) on packed fields for
+ * parity p (0, 1, or 2 = both) and nrhs right-hand sides; out may alias in.
+ * COLA_ERR_UNSUPPORTED without a clover term. */
+cola_status cola_clover_apply(cola_gauge g, void *out, const void *in, int parity, int inverse,
+                              cola_prec prec, int nrhs, cudaStream_t stream);
 
 typedef struct {
     double tol;      /* target true relative residual (e.g. 1e-10) */
@@ -156,7 +196,9 @@ typedef struct {
  * solution.  SYS_NORMAL + OP_FULL: D^dag D x = b.  SYS_NORMAL + OP_EO:
  * Mhat^dag Mhat x_e = b_e (odd sites of b ignored, of x set to zero).
  * SYS_DIRAC: D x = b (OP_EO through the Schur complement and its normal
- * equations, x_o = b_o + kappa H_oe x_e).  info has nrhs entries (host). */
+ * equations, x_o = A_oo^-1 (b_o + kappa H_oe x_e), A = 1 without a clover
+ * term).  info has nrhs entries (host).  With clover terms, every handle of
+ * a batched solve must have one. */
 cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev,
                           const cola_solver_params *params, cola_solve_info *info,
                           cudaStream_t stream);

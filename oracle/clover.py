@@ -131,3 +131,41 @@ def gamma5_commutator(a):
     g5a = np.einsum("su,...uatb->...satb", GAMMA5, a)
     ag5 = np.einsum("...satb,tu->...saub", a, GAMMA5)
     return float(np.max(np.abs(g5a - ag5)))
+
+
+def clover_sites(u, kappa, csw, sites):
+    """A(x) at the listed lexicographic sites i = x + Lx (y + Ly (z + Lz t)), [n, 4, 3, 4, 3].
+
+    Per-site restatement of clover_matrix with explicit coordinate arithmetic
+    (no whole-lattice shifts), for sampled checks on lattices too large for
+    the whole-lattice form.
+    """
+    _, lt, lz, ly, lx = u.shape[:5]
+    dims = (lx, ly, lz, lt)
+
+    def link(c, mu, step):
+        p = [(c[k] + step[k]) % dims[k] for k in range(4)]
+        return u[mu, p[3], p[2], p[1], p[0]]
+
+    out = np.zeros((len(sites), 4, 3, 4, 3), dtype=np.complex128)
+    for n, i in enumerate(sites):
+        i = int(i)
+        c = [i % lx, (i // lx) % ly, (i // (lx * ly)) % lz, i // (lx * ly * lz)]
+        a = np.eye(12, dtype=np.complex128)
+        for mu in range(4):
+            for nu in range(mu + 1, 4):
+                def at(dm, dn, d):
+                    step = [0, 0, 0, 0]
+                    step[mu] += dm
+                    step[nu] += dn
+                    return link(c, mu if d == 0 else nu, step)
+                dg = lambda m: m.conj().T  # noqa: E731
+                q = (at(0, 0, 0) @ at(1, 0, 1) @ dg(at(0, 1, 0)) @ dg(at(0, 0, 1))
+                     + at(0, 0, 1) @ dg(at(-1, 1, 0)) @ dg(at(-1, 0, 1)) @ at(-1, 0, 0)
+                     + dg(at(-1, 0, 0)) @ dg(at(-1, -1, 1)) @ at(-1, -1, 0) @ at(0, -1, 1)
+                     + dg(at(0, -1, 1)) @ at(0, -1, 0) @ at(1, -1, 1) @ dg(at(0, 0, 0)))
+                f = (q - dg(q)) / 8j
+                f = f - np.trace(f) / 3.0 * np.eye(3)
+                a -= kappa * csw * np.kron(SIGMA[mu, nu], f)
+        out[n] = a.reshape(4, 3, 4, 3)
+    return out

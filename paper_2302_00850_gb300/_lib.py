@@ -63,8 +63,12 @@ SIGNATURES = {
     "cola_spinor_pack": (_st, [_vp, _vp, _vp, _i, _i, _vp]),
     "cola_spinor_unpack": (_st, [_vp, _vp, _vp, _i, _i, _vp]),
     "cola_dslash_apply": (_st, [_vp, _vp, _vp, _vp, _d, _d, _i, _i, _i, _i, _vp]),
+    "cola_dirac_apply": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "cola_mdagm_apply": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "cola_mdagm_apply_noalloc": (_st, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "cola_clover_attach": (_st, [_vp, _d, _vp]),
+    "cola_clover_csw": (_d, [_vp]),
+    "cola_clover_apply": (_st, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
     "cola_cg_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_cg_solve_batched": (_st, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                      ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),

@@ -81,6 +81,19 @@ class Gauge:
         check(self.lib.cola_gauge_create(ctypes.byref(self.lat), _complex_field(links, 4 * self.volume * 9, "links"),
                                          ctypes.byref(opts), _stream(self.device), ctypes.byref(self.handle)))
 
+    def attach_clover(self, csw):
+        """Attach the clover term A = 1 - kappa c_sw sum sigma F (csw = 0 removes it).
+
+        Builds A and A^-1 from the FP64 links (the handle must hold "f64");
+        afterwards the Dirac operator, the normal operators and the solves use
+        D = A - kappa H.  Waits for the construction.
+        """
+        check(self.lib.cola_clover_attach(self.handle, float(csw), _stream(self.device)))
+
+    @property
+    def csw(self) -> float:
+        return float(self.lib.cola_clover_csw(self.handle))
+
     def update(self, links):
         """Re-pack new links (same lattice) into this handle, keeping its workspace."""
         check(self.lib.cola_gauge_update(self.handle, _complex_field(links, 4 * self.volume * 9, "links"),
@@ -145,12 +158,35 @@ def mdagm(g: Gauge, out, inp, op="eo", prec="f64", nrhs=1):
     return out
 
 
+def dirac(g: Gauge, out, inp, dagger=False, prec="f64", nrhs=1):
+    """out = D in (or D^dag in) on packed fields; D = A - kappa H with a clover term."""
+    check(g.lib.cola_dirac_apply(g.handle, _ptr(out), _ptr(inp), int(bool(dagger)), PREC[prec], int(nrhs),
+                                 _stream(g.device)))
+    return out
+
+
+def clover(g: Gauge, out, inp, parity=2, inverse=False, prec="f64", nrhs=1):
+    """out_p = A_pp in_p (inverse: A_pp^-1 in_p) on packed fields, parity 0, 1 or 2 = both."""
+    check(g.lib.cola_clover_apply(g.handle, _ptr(out), _ptr(inp), int(parity), int(bool(inverse)), PREC[prec],
+                                  int(nrhs), _stream(g.device)))
+    return out
+
+
 def apply_dirac(g: Gauge, psi: torch.Tensor, dagger=False, prec="f64") -> torch.Tensor:
     """D psi (or D^dag psi) on canonical complex128 fields, through the packed kernels."""
     nrhs = _nrhs_of(g, psi)
     pin = pack(g, psi, prec)
     pout = g.empty_packed(prec, nrhs)
-    dslash(g, pout, pin, pin, a=1.0, b=-g.kappa, parity=2, dagger=dagger, prec=prec, nrhs=nrhs)
+    dirac(g, pout, pin, dagger=dagger, prec=prec, nrhs=nrhs)
+    return unpack(g, pout, prec, None if psi.dim() == 6 else nrhs).reshape(psi.shape)
+
+
+def apply_clover(g: Gauge, psi: torch.Tensor, inverse=False, prec="f64") -> torch.Tensor:
+    """A psi (or A^-1 psi) on canonical complex128 fields, through the packed kernels."""
+    nrhs = _nrhs_of(g, psi)
+    pin = pack(g, psi, prec)
+    pout = g.empty_packed(prec, nrhs)
+    clover(g, pout, pin, parity=2, inverse=inverse, prec=prec, nrhs=nrhs)
     return unpack(g, pout, prec, None if psi.dim() == 6 else nrhs).reshape(psi.shape)
 
 

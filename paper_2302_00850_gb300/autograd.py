@@ -24,11 +24,17 @@ def _gauge(links, dims, kappa, bc, precisions=("f64",)):
 
 
 class DiracOp(torch.autograd.Function):
-    """y = D[U] psi on canonical complex128 fields."""
+    """y = D[U] psi on canonical complex128 fields (csw != 0: D = A - kappa H).
+
+    With a clover term only the gradient with respect to psi is available
+    (the link gradient of the clover term is not implemented and raises).
+    """
 
     @staticmethod
-    def forward(ctx, links, psi, dims, kappa, bc):
+    def forward(ctx, links, psi, dims, kappa, bc, csw=0.0):
         g = _gauge(links, dims, kappa, bc)
+        if csw:
+            g.attach_clover(csw)
         psi_c = psi.detach().contiguous()
         y = apply_dirac(g, psi_c)
         ctx.save_for_backward(psi_c)
@@ -42,7 +48,7 @@ class DiracOp(torch.autograd.Function):
         gy = gy.contiguous()
         grad_links = dirac_link_grad(g, psi, gy) if ctx.needs_input_grad[0] else None
         grad_psi = apply_dirac(g, gy, dagger=True) if ctx.needs_input_grad[1] else None
-        return grad_links, grad_psi, None, None, None
+        return grad_links, grad_psi, None, None, None, None
 
 
 def _solve(g, rhs, tol, inner):

@@ -159,14 +159,21 @@ DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, c
     return A;
 }
 
-cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
+cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, int epi,
                           cudaStream_t s) {
-    return cuda_check(launch_dslash(prec, owner->recon[prec], A, nparity, dagger, xpay, 0, s), "dslash launch");
+    return cuda_check(launch_dslash(prec, owner->recon[prec], A, nparity, dagger, epi, 0, s), "dslash launch");
 }
 
+// With a clover term (every lattice of the batch has one, or none does):
+//   Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe,  D = A - kappa H,
+// the A_oo^-1 riding on the odd-parity hops (EPI_CLOVER_INV) and A on the
+// xpay term (EPI_CLOVER_X); the sequence of launches is the same.
 cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
                               cudaStream_t s) {
     cola_gauge owner = L[0].g;
+    const bool clv = owner->csw != 0.0;
+    const int epi_x = clv ? EPI_CLOVER_X : EPI_XPAY;
+    const int epi_h = clv ? EPI_CLOVER_INV : EPI_HOP;
     auto batch = [&](int parity0, double a_coef, bool use_xin, int which) {
         // which: 0 in->t, 1 t->mp (xin = in), 2 mp->t, 3 t->out (xin = mp); full: 4 in->mp, 5 mp->out
         DslashArgs A = empty_args(nrhs, parity0);
@@ -181,23 +188,24 @@ cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nr
             const void *in = which == 0 || which == 4 ? o.in : which == 1 || which == 3 ? o.t : o.mp;
             const void *xin = !use_xin ? nullptr : (which == 1 || which == 4) ? o.in : o.mp;
             A.lat[l] = make_dslash_lat(o.g, prec, out, in, xin, a_coef, b, o.row0);
+            if (clv) set_clover(A.lat[l], o.g, prec, !use_xin);
         }
         return A;
     };
     if (op == COLA_OP_EO) {
         DslashArgs A = batch(1, 0.0, false, 0);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, false, false, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, epi_h, s));
         A = batch(0, 1.0, true, 1);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, false, true, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, false, epi_x, s));
         A = batch(1, 0.0, false, 2);
-        COLA_TRY(dslash_launch(owner, prec, A, 1, true, false, s));
+        COLA_TRY(dslash_launch(owner, prec, A, 1, true, epi_h, s));
         A = batch(0, 1.0, true, 3);
-        return dslash_launch(owner, prec, A, 1, true, true, s);
+        return dslash_launch(owner, prec, A, 1, true, epi_x, s);
     }
     DslashArgs A = batch(0, 1.0, true, 4);
-    COLA_TRY(dslash_launch(owner, prec, A, 2, false, true, s));
+    COLA_TRY(dslash_launch(owner, prec, A, 2, false, epi_x, s));
     A = batch(0, 1.0, true, 5);
-    return dslash_launch(owner, prec, A, 2, true, true, s);
+    return dslash_launch(owner, prec, A, 2, true, epi_x, s);
 }
 
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
@@ -209,6 +217,16 @@ cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *i
 }  // namespace cola
 
 using namespace cola;
+
+static cola_status check_rhs(int nrhs) {
+    if (nrhs < 1 || nrhs > 65535) return arg_error("nrhs must be in 1..65535");
+    return COLA_OK;
+}
+
+static cola_status clover_unsupported(const char *what) {
+    set_error(std::string(what) + " differentiates the Wilson hopping term only; the handle has a clover term");
+    return COLA_ERR_UNSUPPORTED;
+}
 
 extern "C" {
 
@@ -256,7 +274,44 @@ cola_status cola_gauge_update(cola_gauge g, const void *links_dev, cudaStream_t 
         if (g->links[p])
             COLA_TRY(cuda_check(launch_pack_gauge(p, g->recon[p], g->geom, g->links[p], links_dev, stream),
                                 "link packing"));
+    if (g->csw != 0.0) return clover_rebuild(g, stream);
     return COLA_OK;
+}
+
+cola_status cola_clover_attach(cola_gauge g, double csw, cudaStream_t stream) {
+    if (!g) return arg_error("null gauge handle");
+    if (!std::isfinite(csw)) return arg_error("c_sw is not finite");
+    if (csw == 0.0) {
+        cudaStreamSynchronize(stream);
+        clover_free(g);
+        return COLA_OK;
+    }
+    g->csw = csw;
+    cola_status st = clover_rebuild(g, stream);
+    if (st != COLA_OK) {
+        const std::string msg = cola_last_error();
+        cudaStreamSynchronize(stream);
+        clover_free(g);
+        set_error(msg);
+    }
+    return st;
+}
+
+double cola_clover_csw(cola_gauge g) { return g ? g->csw : 0.0; }
+
+cola_status cola_clover_apply(cola_gauge g, void *out, const void *in, int parity, int inverse, cola_prec prec,
+                              int nrhs, cudaStream_t stream) {
+    if (!g || !out || !in) return arg_error("null argument to cola_clover_apply");
+    if (parity < 0 || parity > 2) return arg_error("parity must be 0, 1 or 2");
+    COLA_TRY(check_prec(g, prec));
+    COLA_TRY(check_rhs(nrhs));
+    if (g->csw == 0.0) {
+        set_error("no clover term is attached to this gauge handle");
+        return COLA_ERR_UNSUPPORTED;
+    }
+    const void *c = inverse ? g->clover_inv[prec] : g->clover[prec];
+    return cuda_check(launch_clover_apply(prec, g->geom, c, out, in, nrhs, parity == 2 ? 3 : 1 << parity, stream),
+                      "clover apply");
 }
 
 cola_status cola_gauge_destroy(cola_gauge g) {
@@ -264,6 +319,7 @@ cola_status cola_gauge_destroy(cola_gauge g) {
     cudaDeviceSynchronize();
     for (int p = 0; p < 3; ++p)
         if (g->links[p]) cudaFree(g->links[p]);
+    clover_free(g);
     for (int k = 0; k < cola_gauge_s::kSlots; ++k)
         if (g->slot[k]) cudaFree(g->slot[k]);
     if (g->partials) cudaFree(g->partials);
@@ -274,10 +330,6 @@ cola_status cola_gauge_destroy(cola_gauge g) {
     return COLA_OK;
 }
 
-static cola_status check_rhs(int nrhs) {
-    if (nrhs < 1 || nrhs > 65535) return arg_error("nrhs must be in 1..65535");
-    return COLA_OK;
-}
 
 cola_status cola_spinor_pack(cola_gauge g, void *packed_dev, const void *canon_dev, cola_prec prec, int nrhs,
                              cudaStream_t stream) {
@@ -309,6 +361,17 @@ cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const voi
     return dslash_launch(g, prec, A, parity == 2 ? 2 : 1, dagger != 0, xpay, stream);
 }
 
+cola_status cola_dirac_apply(cola_gauge g, void *out, const void *in, int dagger, cola_prec prec, int nrhs,
+                             cudaStream_t stream) {
+    if (!g || !out || !in) return arg_error("null argument to cola_dirac_apply");
+    if (out == in) return arg_error("out must not alias in");
+    COLA_TRY(check_prec(g, prec));
+    COLA_TRY(check_rhs(nrhs));
+    DslashArgs A = make_dslash_args(g, prec, out, in, in, nrhs, 0, 1.0, -g->lat.kappa);
+    if (g->csw != 0.0) set_clover(A.lat[0], g, prec, false);
+    return dslash_launch(g, prec, A, 2, dagger != 0, g->csw != 0.0 ? EPI_CLOVER_X : EPI_XPAY, stream);
+}
+
 cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec, int nrhs,
                              cudaStream_t stream) {
     if (!g || !out || !in) return arg_error("null argument to cola_mdagm_apply");
@@ -327,6 +390,7 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
                                cudaStream_t stream) {
     if (!g || !force_dev || !X_dev || !Y_dev) return arg_error("null argument to cola_fermion_force");
     COLA_TRY(check_prec(g, COLA_F64));
+    if (g->csw != 0.0) return clover_unsupported("cola_fermion_force");
     return cuda_check(launch_force(g->geom, g->lat.kappa, g->links[COLA_F64], g->recon[COLA_F64], force_dev, X_dev,
                                    Y_dev, stream),
                       "force launch");
@@ -335,6 +399,7 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
 cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev, const void *gy_dev,
                                  cudaStream_t stream) {
     if (!g || !grad_links_dev || !psi_dev || !gy_dev) return arg_error("null argument to cola_dirac_link_grad");
+    if (g->csw != 0.0) return clover_unsupported("cola_dirac_link_grad");
     return cuda_check(launch_link_grad(g->geom, g->lat.kappa, grad_links_dev, psi_dev, gy_dev, stream),
                       "link gradient launch");
 }

@@ -22,6 +22,8 @@ struct DslashLat {
     void *out;
     const void *in;
     const void *xin;              // xpay input, same layout as out (null if !xpay)
+    const void *clv;              // clover field of the epilogue (A or A^-1, both parities), else null
+    size_t clv_parity_stride;     // bytes of one parity of clv
     size_t parity_stride;         // bytes of one parity of one spinor field
     size_t rhs_stride;            // bytes of one right-hand side of a spinor field
     double a, b;                  // out = a xin + b H in
@@ -41,6 +43,13 @@ struct DslashArgs {
     int ngroups;                  // right-hand-side groups (set by launch_dslash)
 };
 
+// Epilogue of a hopping-term launch, per output site x of parity p:
+//   EPI_HOP         out = b H in
+//   EPI_XPAY        out = a xin + b H in
+//   EPI_CLOVER_X    out = a A(x) xin + b H in          (clv = A)
+//   EPI_CLOVER_INV  out = A(x)^-1 (b H in)              (clv = A^-1)
+enum DslashEpi : int { EPI_HOP = 0, EPI_XPAY = 1, EPI_CLOVER_X = 2, EPI_CLOVER_INV = 3 };
+
 int default_dslash_block(int prec, int rhs_per_block);
 // Within this scope (per thread), launch_dslash only autotunes configurations
 // it has not seen and launches nothing else.
@@ -50,8 +59,27 @@ struct TuneOnlyScope {
 };
 // Fills block0/nblocks of every lattice and launches; block_x <= 0 picks the
 // autotuned (or default) launch shape.
-cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, bool xpay, int block_x,
+cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool dagger, int epi, int block_x,
                           cudaStream_t s);
+// The clover epilogues (instantiated in their own translation unit); A's
+// block0/nblocks/ngroups are already assigned, nb is the grid size.
+cudaError_t launch_dslash_clover(int prec, int recon, const DslashArgs &A, int nparity, bool dagger, int epi, int bx,
+                                 int nb, cudaStream_t s);
+
+// ----------------------------------------------------------------- clover --
+// sigma_munu restricted to the two chirality blocks, planes in the order
+// (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): sig[plane][chi][2 s + t] = (re, im).
+struct CloverSigma {
+    double v[6][2][4][2];
+};
+// Builds A = 1 - coef sum sigma F and A^-1 (coef = kappa c_sw) on every site
+// from the FP64 links and writes both into each non-null a[p] / ainv[p];
+// *bad is set to 1 if a block of A has a zero or non-finite pivot.
+cudaError_t launch_clover_build(const Geom &g, const void *links_f64, int recon, double coef, const CloverSigma &sig,
+                                void *const a[3], void *const ainv[3], int *bad, cudaStream_t s);
+// out_p = C_p in_p on the parities of parity_mask (1 even, 2 odd, 3 both).
+cudaError_t launch_clover_apply(int prec, const Geom &g, const void *clv, void *out, const void *in, int nrhs,
+                                int parity_mask, cudaStream_t s);
 
 // ---------------------------------------------------------------- packing --
 cudaError_t launch_pack_gauge(int prec, int recon, const Geom &g, void *packed, const void *canon,
@@ -124,10 +152,15 @@ struct cola_gauge_s {
     cola::Geom geom;
     int device = 0;
     void *links[3] = {nullptr, nullptr, nullptr};  // [parity][mu][group][Vh] per precision
+    // clover term (csw != 0): A and A^-1 in every precision of the links
+    double csw = 0.0;
+    void *clover[3] = {nullptr, nullptr, nullptr};
+    void *clover_inv[3] = {nullptr, nullptr, nullptr};
     int recon[3] = {12, 12, 12};
     size_t link_parity_bytes[3] = {0, 0, 0};
     // workspace slots: each a device buffer reused across calls
     static constexpr int kSlots = 24;
+    static constexpr int kSlotCloverFlag = kSlots - 1;  // the construction's pivot flag
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     double *partials = nullptr;
@@ -163,9 +196,16 @@ DslashLat make_dslash_lat(cola_gauge g, int prec, void *out, const void *in, con
                           int row0);
 DslashArgs make_dslash_args(cola_gauge g, int prec, void *out, const void *in, const void *xin, int nrhs,
                             int parity0, double a, double b);
+// Sets L's epilogue clover field to g's A (inverse: A^-1) of precision prec.
+void set_clover(DslashLat &L, cola_gauge g, int prec, bool inverse);
 // Launch a (batched) hopping term with the links of `owner`'s reconstruction.
-cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, bool xpay,
+cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, int epi,
                           cudaStream_t s);
+// (Re)builds g's clover fields from its FP64 links (g->csw != 0); waits for
+// the construction to read its pivot flag.
+cola_status clover_rebuild(cola_gauge g, cudaStream_t s);
+// Frees g's clover fields and sets g->csw = 0.
+void clover_free(cola_gauge g);
 // out = Mdag M in for every lattice of L (op EO: Mhat on even halves, with
 // Mhat in left in mp; op FULL: D, with D in left in mp).  With st != nullptr
 // rows are filtered by st (filter_ru: only rows with a pending reliable

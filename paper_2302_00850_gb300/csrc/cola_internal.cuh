@@ -352,6 +352,126 @@ struct LinkIO<COLA_F16, RECON> {
     }
 };
 
+// ---------------------------------------------------------- clover access --
+// The clover matrix A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_munu F_munu(x)
+// (or its inverse) commutes with gamma5 = diag(1, 1, -1, -1), so it is two
+// Hermitian 6x6 blocks per site: chirality 0 acts on spins 0, 1 and
+// chirality 1 on spins 2, 3, with block row 3 (spin mod 2) + colour, i.e.
+// components 6 chi .. 6 chi + 5 of a spinor.  A block is stored as 36 reals:
+// the 6 (real) diagonal entries, then the 15 entries below the diagonal row
+// by row, (1,0) (2,0) (2,1) (3,0) ... (5,4), each as (re, im).
+// Layout: [parity][chirality][group][Vh]; a group holds 2 reals (F64,
+// double2), 4 reals (F32, float4) or 4 halves (F16, uint2: no scale, the
+// entries of A and of a well-conditioned A^-1 are O(1)).
+constexpr int kCloverReals = 36;
+
+__host__ __device__ constexpr size_t clover_block_bytes(int prec, int vh) {
+    return (size_t)kCloverReals * (prec == COLA_F64 ? 8 : prec == COLA_F32 ? 4 : 2) * vh;
+}
+__host__ __device__ constexpr size_t clover_parity_bytes(int prec, int vh) { return 2 * clover_block_bytes(prec, vh); }
+
+template <int P>
+struct CloverIO;
+
+template <>
+struct CloverIO<COLA_F64> {
+    __device__ static __forceinline__ void load(const void *blk, int vh, int cb, double (&m)[kCloverReals]) {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 2; ++k) {
+            const double2 v = __ldg(p + (size_t)k * vh + cb);
+            m[2 * k] = v.x;
+            m[2 * k + 1] = v.y;
+        }
+    }
+    __device__ static __forceinline__ void store(void *blk, int vh, int cb, const double (&m)[kCloverReals]) {
+        double2 *p = reinterpret_cast<double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 2; ++k) p[(size_t)k * vh + cb] = make_double2(m[2 * k], m[2 * k + 1]);
+    }
+};
+
+template <>
+struct CloverIO<COLA_F32> {
+    __device__ static __forceinline__ void load(const void *blk, int vh, int cb, float (&m)[kCloverReals]) {
+        const float4 *p = reinterpret_cast<const float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 4; ++k) {
+            const float4 v = __ldg(p + (size_t)k * vh + cb);
+            m[4 * k] = v.x;
+            m[4 * k + 1] = v.y;
+            m[4 * k + 2] = v.z;
+            m[4 * k + 3] = v.w;
+        }
+    }
+    __device__ static __forceinline__ void store(void *blk, int vh, int cb, const double (&m)[kCloverReals]) {
+        float4 *p = reinterpret_cast<float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 4; ++k)
+            p[(size_t)k * vh + cb] = make_float4((float)m[4 * k], (float)m[4 * k + 1], (float)m[4 * k + 2],
+                                                 (float)m[4 * k + 3]);
+    }
+};
+
+template <>
+struct CloverIO<COLA_F16> {
+    __device__ static __forceinline__ void load(const void *blk, int vh, int cb, float (&m)[kCloverReals]) {
+        const uint2 *p = reinterpret_cast<const uint2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 4; ++k) {
+            const uint2 v = __ldg(p + (size_t)k * vh + cb);
+            const float2 a = h2f(v.x), b = h2f(v.y);
+            m[4 * k] = a.x;
+            m[4 * k + 1] = a.y;
+            m[4 * k + 2] = b.x;
+            m[4 * k + 3] = b.y;
+        }
+    }
+    __device__ static __forceinline__ void store(void *blk, int vh, int cb, const double (&m)[kCloverReals]) {
+        uint2 *p = reinterpret_cast<uint2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < kCloverReals / 4; ++k) {
+            uint2 v;
+            v.x = f2h((float)m[4 * k], (float)m[4 * k + 1]);
+            v.y = f2h((float)m[4 * k + 2], (float)m[4 * k + 3]);
+            p[(size_t)k * vh + cb] = v;
+        }
+    }
+};
+
+// o = M v for one Hermitian block in the packed form above.
+template <typename R>
+__device__ __forceinline__ void herm6_mul(const R (&m)[kCloverReals], const Cx<R> *v, Cx<R> (&o)[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[i] = {m[i] * v[i].re, m[i] * v[i].im};
+    int k = 6;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const Cx<R> l = {m[k], m[k + 1]};
+            k += 2;
+            cmac(o[i], l, v[j]);       // below the diagonal: M_ij = l
+            cmac_conj(o[j], l, v[i]);  // above it: M_ji = conj(l)
+        }
+}
+
+// v <- C v for the clover field C (A or A^-1) of one parity at site cb.
+template <int P>
+__device__ __forceinline__ void clover_mul(const char *parity_base, int vh, int cb,
+                                           Cx<typename Prec<P>::real> (&v)[12]) {
+    using R = typename Prec<P>::real;
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        R m[kCloverReals];
+        CloverIO<P>::load(parity_base + chi * clover_block_bytes(P, vh), vh, cb, m);
+        Cx<R> o[6];
+        herm6_mul(m, v + 6 * chi, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[6 * chi + i] = o[i];
+    }
+}
+
 }  // namespace cola
 
 namespace cola {

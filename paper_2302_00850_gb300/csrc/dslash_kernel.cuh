@@ -1,0 +1,594 @@
+// Hopping-term kernel templates (the fermion-matrix kernel), included by the
+// translation units that instantiate them: dslash.cu (plain and xpay
+// epilogues, launch shapes, autotuning) and dslash_clover.cu (clover
+// epilogues).
+//
+// Wilson hopping term on checkerboarded fields (the fermion-matrix kernel).
+//
+// The paper maps one lattice site to one GPU thread and notes that lattice
+// codes are memory-bandwidth bound, so spending arithmetic to save traffic
+// pays (its discussion of the GPU inverter).  This kernel follows that: one
+// thread per output site and right-hand side; links stored as two rows and
+// the third rebuilt in registers (recon 12); spinors in a structure-of-arrays
+// checkerboard layout so that each 16-byte load of a warp is coalesced;
+// FP16 storage with a per-site scale for the inner solver.
+//
+// For output parity p and each direction mu:
+//   forward : (1 - s gamma_mu) Ut_mu(x) psi(x + mu)
+//   backward: (1 + s gamma_mu) Ut_mu(x - mu)^dag psi(x - mu)
+// with s = +1 for H and s = -1 for H^dag (projectors swapped).  Each
+// projector has rank two, so the SU(3) multiply acts on a two-spinor and
+// the other two spin rows are rebuilt from it (spin projection and
+// reconstruction, gamma matrices in the DeGrand-Rossi basis).
+#pragma once
+
+#include "cola_impl.h"
+
+#ifndef COLA_DSLASH_MINB
+#define COLA_DSLASH_MINB 2
+#endif
+
+namespace cola {
+
+// a + s*i*b
+template <typename R, int S>
+__device__ __forceinline__ Cx<R> add_si(Cx<R> a, Cx<R> b) {
+    if constexpr (S > 0) return {a.re - b.im, a.im + b.re};
+    else return {a.re + b.im, a.im - b.re};
+}
+template <typename R, int S>
+__device__ __forceinline__ Cx<R> add_s(Cx<R> a, Cx<R> b) {
+    if constexpr (S > 0) return {a.re + b.re, a.im + b.im};
+    else return {a.re - b.re, a.im - b.im};
+}
+
+// Two-spinor h = rows 0, 1 of (1 + S gamma_mu) psi.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Cx<R> (&psi)[12], Cx<R> (&h)[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const Cx<R> p0 = psi[a], p1 = psi[3 + a], p2 = psi[6 + a], p3 = psi[9 + a];
+        if constexpr (MU == 0) {         // gamma_x psi = (i p3, i p2, -i p1, -i p0)
+            h[0][a] = add_si<R, S>(p0, p3);
+            h[1][a] = add_si<R, S>(p1, p2);
+        } else if constexpr (MU == 1) {  // gamma_y psi = (-p3, p2, p1, -p0)
+            h[0][a] = add_s<R, -S>(p0, p3);
+            h[1][a] = add_s<R, S>(p1, p2);
+        } else if constexpr (MU == 2) {  // gamma_z psi = (i p2, -i p3, -i p0, i p1)
+            h[0][a] = add_si<R, S>(p0, p2);
+            h[1][a] = add_si<R, -S>(p1, p3);
+        } else {                         // gamma_t psi = (p2, p3, p0, p1)
+            h[0][a] = add_s<R, S>(p0, p2);
+            h[1][a] = add_s<R, S>(p1, p3);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> times_i(Cx<R> a, int s) {  // s*i*a
+    return s > 0 ? Cx<R>{-a.im, a.re} : Cx<R>{a.im, -a.re};
+}
+
+// acc += sc * (full spinor rebuilt from w = U h); rows 2, 3 follow from rows 0, 1.
+// sc carries the neighbour's FP16 site scale and a real boundary phase, so
+// both cost nothing beyond the fused multiply-adds of the accumulation.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3], R sc) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a].re = fma(sc, w[0][a].re, acc[a].re);
+        acc[a].im = fma(sc, w[0][a].im, acc[a].im);
+        acc[3 + a].re = fma(sc, w[1][a].re, acc[3 + a].re);
+        acc[3 + a].im = fma(sc, w[1][a].im, acc[3 + a].im);
+        if constexpr (MU == 0) {         // r2 = -S i w1, r3 = -S i w0;  i(x + iy) = -y + ix
+            acc[6 + a].re = fma(S * sc, w[1][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, w[1][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, w[0][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, w[0][a].re, acc[9 + a].im);
+        } else if constexpr (MU == 1) {  // r2 = S w1, r3 = -S w0
+            acc[6 + a].re = fma(S * sc, w[1][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, w[1][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, w[0][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, w[0][a].im, acc[9 + a].im);
+        } else if constexpr (MU == 2) {  // r2 = -S i w0, r3 = S i w1
+            acc[6 + a].re = fma(S * sc, w[0][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, w[0][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, w[1][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, w[1][a].re, acc[9 + a].im);
+        } else {                         // r2 = S w0, r3 = S w1
+            acc[6 + a].re = fma(S * sc, w[0][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, w[0][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, w[1][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, w[1][a].im, acc[9 + a].im);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[2][3], Cx<R> (&w)[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Cx<R> s = cmul(u[3 * a], h[k][0]);
+            cmac(s, u[3 * a + 1], h[k][1]);
+            cmac(s, u[3 * a + 2], h[k][2]);
+            w[k][a] = s;
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[2][3], Cx<R> (&w)[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Cx<R> s = {R(0), R(0)};
+            cmac_conj(s, u[a], h[k][0]);
+            cmac_conj(s, u[3 + a], h[k][1]);
+            cmac_conj(s, u[6 + a], h[k][2]);
+            w[k][a] = s;
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void phase_mul(Cx<R> (&w)[2][3], R pr, R pi) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w[k][a] = cmul(w[k][a], Cx<R>{pr, pi});
+}
+
+// Scale of a hop crossing the boundary: a real phase folds into sc, a
+// complex one multiplies w.
+template <typename R>
+__device__ __forceinline__ void boundary_phase(const Geom &g, int mu, bool conj_phase, Cx<R> (&w)[2][3], R &sc) {
+    const R pr = (R)g.bc[mu][0];
+    const R pi = conj_phase ? -(R)g.bc[mu][1] : (R)g.bc[mu][1];
+    if (pi == R(0)) sc *= pr;
+    else phase_mul(w, pr, pi);
+}
+
+// Rows 0 and 1 of acc += sc * c (no reconstruction: c is a sum of hops).
+template <typename R>
+__device__ __forceinline__ void accumulate01(Cx<R> (&acc)[12], const Cx<R> (&c)[2][3], R sc) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a].re = fma(sc, c[0][a].re, acc[a].re);
+        acc[a].im = fma(sc, c[0][a].im, acc[a].im);
+        acc[3 + a].re = fma(sc, c[1][a].re, acc[3 + a].re);
+        acc[3 + a].im = fma(sc, c[1][a].im, acc[3 + a].im);
+    }
+}
+
+// Rows 2 and 3 of the reconstruction of d with projector sign S, times sc.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate23(Cx<R> (&acc)[12], const Cx<R> (&d)[2][3], R sc) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (MU == 0) {
+            acc[6 + a].re = fma(S * sc, d[1][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, d[1][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, d[0][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, d[0][a].re, acc[9 + a].im);
+        } else if constexpr (MU == 1) {
+            acc[6 + a].re = fma(S * sc, d[1][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, d[1][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, d[0][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(-S * sc, d[0][a].im, acc[9 + a].im);
+        } else if constexpr (MU == 2) {
+            acc[6 + a].re = fma(S * sc, d[0][a].im, acc[6 + a].re);
+            acc[6 + a].im = fma(-S * sc, d[0][a].re, acc[6 + a].im);
+            acc[9 + a].re = fma(-S * sc, d[1][a].im, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, d[1][a].re, acc[9 + a].im);
+        } else {
+            acc[6 + a].re = fma(S * sc, d[0][a].re, acc[6 + a].re);
+            acc[6 + a].im = fma(S * sc, d[0][a].im, acc[6 + a].im);
+            acc[9 + a].re = fma(S * sc, d[1][a].re, acc[9 + a].re);
+            acc[9 + a].im = fma(S * sc, d[1][a].im, acc[9 + a].im);
+        }
+    }
+}
+
+// c += U^dag h (continues the multiply-add chains that produced c).
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul_add(const Cx<R> (&u)[9], const Cx<R> (&h)[2][3], Cx<R> (&c)[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cmac_conj(c[k][a], u[a], h[k][0]);
+            cmac_conj(c[k][a], u[3 + a], h[k][1]);
+            cmac_conj(c[k][a], u[6 + a], h[k][2]);
+        }
+}
+
+// Both hops of direction mu, results scaled by bs (the output factor b).
+// The forward and backward reconstructions differ only in the sign of their
+// lower two rows, so away from the boundary both hops enter as
+//   rows 0,1 += bs (w_f + w_b),   rows 2,3 += bs C_f (w_f - w_b),
+// with c = w_f + w_b built by continuing w_f's multiply-add chains and
+// w_f - w_b = 2 w_f - c: twelve multiply-adds fewer than two full
+// reconstructions.  Hops that cross the boundary (phase) or carry an FP16
+// site scale take the general form.
+template <int P, int RECON, int MU, bool DAGGER>
+__device__ __forceinline__ void hop_mu(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                       const char *links_out, const char *links_in,
+                                       Cx<typename Prec<P>::real> (&acc)[12], typename Prec<P>::real bs) {
+    using R = typename Prec<P>::real;
+    const Geom &g = A.g;
+    constexpr int SF = DAGGER ? +1 : -1;  // forward projector 1 + SF gamma
+    constexpr int SB = -SF;
+    const int nbf = nbr_cb<MU, +1>(g, c, cb);
+    const int nbb = nbr_cb<MU, -1>(g, c, cb);
+    Cx<R> hf[2][3], hb[2][3], uf[9], ub[9];
+    R scf, scb;
+    {
+        Cx<R> psi[12];
+        scf = SpinorIO<P>::load_raw(in, g.Vh, nbf, psi);
+        project<MU, SF>(psi, hf);
+    }
+    LinkIO<P, RECON>::load(links_out + MU * A.link_dir_stride, g.Vh, cb, uf);
+    {
+        Cx<R> psi[12];
+        scb = SpinorIO<P>::load_raw(in, g.Vh, nbb, psi);
+        project<MU, SB>(psi, hb);
+    }
+    LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nbb, ub);
+    const bool edge_f = !g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1;
+    const bool edge_b = !g.bc_trivial[MU] && coord_of<MU>(c) == 0;
+    Cx<R> wf[2][3];
+    su3_mul(uf, hf, wf);
+    if (P != COLA_F16 && !edge_f && !edge_b) {
+        Cx<R> cs[2][3];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cs[k][a] = wf[k][a];
+        su3_adj_mul_add(ub, hb, cs);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                wf[k][a].re = fma(R(2), wf[k][a].re, -cs[k][a].re);
+                wf[k][a].im = fma(R(2), wf[k][a].im, -cs[k][a].im);
+            }
+        accumulate01(acc, cs, bs);
+        accumulate23<MU, SF>(acc, wf, bs);
+    } else {
+        R sf = scf * bs, sb = scb * bs;
+        if (edge_f) boundary_phase(g, MU, false, wf, sf);
+        accumulate<MU, SF>(acc, wf, sf);
+        Cx<R> wb[2][3];
+        su3_adj_mul(ub, hb, wb);
+        if (edge_b) boundary_phase(g, MU, true, wb, sb);
+        accumulate<MU, SB>(acc, wb, sb);
+    }
+}
+
+// ------------------------------------------------------------------ staged --
+// The FP16/FP32 kernels are limited by how many bytes each SM keeps in
+// flight, not by arithmetic: a thread that loads one hop at a time leaves
+// HBM idle.  The staged variant has each thread copy the raw bytes of its
+// next NSTAGE-1 hops (neighbour spinor, its FP16 scale, the link) into its
+// own shared-memory slots with asynchronous copies (cp.async), then computes
+// hop j from shared memory while hops j+1.. are in flight.  Copies do not
+// occupy registers, so the pipeline depth is not bounded by the register
+// file.  Each thread reads only what it copied itself, so completion needs
+// cp.async.wait_group only, no block barrier.  Shared layout per stage:
+// [chunk][thread] so that a warp's 16-byte reads are conflict-free.
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Raw bytes of one hop: spinor chunks of 16 B (+ one 4-byte FP16 scale) and
+// link chunks of 16 B (FP32) or 8 B (FP16).
+template <int P, int RECON>
+struct HopLayout {
+    static constexpr int spin16 = P == COLA_F32 ? 6 : 3;
+    static constexpr int scale4 = P == COLA_F16 ? 1 : 0;
+    static constexpr int link_chunks = RECON == 12 ? 3 : 5;
+    static constexpr int link_bytes = P == COLA_F32 ? 16 : 8;
+    static constexpr int bytes = spin16 * 16 + scale4 * 4 + link_chunks * link_bytes;
+};
+
+// The staged kernel always runs kStagedThreads threads per block (sites x
+// right-hand sides), so every shared-memory offset is a compile-time constant
+// plus one per-thread term.
+constexpr int kStagedThreads = 128;
+
+template <int P, int RECON>
+struct Stage {
+    using L = HopLayout<P, RECON>;
+    static constexpr int T = kStagedThreads;
+    char *base;  // this stage's area
+    __device__ uint4 *spin(int k, int tid) const { return reinterpret_cast<uint4 *>(base) + k * T + tid; }
+    __device__ float *scale(int tid) const {
+        return reinterpret_cast<float *>(base + L::spin16 * 16 * T) + tid;
+    }
+    __device__ char *link(int k, int tid) const {
+        return base + (L::spin16 * 16 + L::scale4 * 4) * T + (k * T + tid) * L::link_bytes;
+    }
+};
+
+// hop j = 2*mu + (0 forward, 1 backward)
+template <int J>
+struct Hop {
+    static constexpr int MU = J / 2;
+    static constexpr int DIR = (J % 2 == 0) ? +1 : -1;
+};
+
+template <int P, int RECON, int J>
+__device__ __forceinline__ void stage_issue(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *links_out, const char *links_in, const Stage<P, RECON> &st,
+                                            int tid) {
+    using L = HopLayout<P, RECON>;
+    constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
+    const Geom &g = A.g;
+    const int nb = nbr_cb<MU, DIR>(g, c, cb);
+#pragma unroll
+    for (int k = 0; k < L::spin16; ++k) cp_async16(st.spin(k, tid), in + ((size_t)k * g.Vh + nb) * 16);
+    if constexpr (L::scale4) cp_async4(st.scale(tid), in + (size_t)L::spin16 * 16 * g.Vh + (size_t)nb * 4);
+    const char *lb = (DIR > 0 ? links_out : links_in) + MU * A.link_dir_stride;
+    const int lcb = DIR > 0 ? cb : nb;
+#pragma unroll
+    for (int k = 0; k < L::link_chunks; ++k) {
+        const char *src = lb + ((size_t)k * g.Vh + lcb) * L::link_bytes;
+        if constexpr (L::link_bytes == 16) cp_async16(st.link(k, tid), src);
+        else cp_async8(st.link(k, tid), src);
+    }
+}
+
+template <int P, int RECON, int J, bool DAGGER>
+__device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c, const Stage<P, RECON> &st,
+                                              int tid, Cx<float> (&acc)[12], float bs) {
+    using L = HopLayout<P, RECON>;
+    constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
+    constexpr int SF = DAGGER ? +1 : -1;
+    constexpr int S = DIR > 0 ? SF : -SF;
+    const Geom &g = A.g;
+    Cx<float> psi[12];
+    float sc = bs;
+    if constexpr (P == COLA_F16) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 v = *st.spin(k, tid);
+            float2 a = h2f(v.x), b = h2f(v.y), cc = h2f(v.z), d = h2f(v.w);
+            psi[4 * k + 0] = {a.x, a.y};
+            psi[4 * k + 1] = {b.x, b.y};
+            psi[4 * k + 2] = {cc.x, cc.y};
+            psi[4 * k + 3] = {d.x, d.y};
+        }
+        sc *= *st.scale(tid);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(st.spin(k, tid));
+            psi[2 * k] = {v.x, v.y};
+            psi[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    Cx<float> h[2][3];
+    project<MU, S>(psi, h);
+    Cx<float> u[9];
+    if constexpr (P == COLA_F16) {
+#pragma unroll
+        for (int k = 0; k < L::link_chunks; ++k) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(st.link(k, tid));
+            float2 a = h2f(v.x), b = h2f(v.y);
+            if (2 * k < 9) u[2 * k] = {a.x, a.y};
+            if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::link_chunks; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(st.link(k, tid));
+            if (2 * k < 9) u[2 * k] = {v.x, v.y};
+            if (2 * k + 1 < 9) u[2 * k + 1] = {v.z, v.w};
+        }
+    }
+    if constexpr (RECON == 12) reconstruct_row2(u);
+    Cx<float> w[2][3];
+    if constexpr (DIR > 0) su3_mul(u, h, w);
+    else su3_adj_mul(u, h, w);
+    if (!g.bc_trivial[MU] && coord_of<MU>(c) == (DIR > 0 ? g.L[MU] - 1 : 0)) boundary_phase(g, MU, DIR < 0, w, sc);
+    accumulate<MU, S>(acc, w, sc);
+}
+
+template <int P, int RECON, bool DAGGER, int NS, int J>
+__device__ __forceinline__ void staged_step(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *lo, const char *li, char *smem, int T, int tid,
+                                            Cx<float> (&acc)[12], float bs) {
+    using L = HopLayout<P, RECON>;
+    if constexpr (J + NS - 1 < 8) {
+        Stage<P, RECON> nx{smem + ((J + NS - 1) % NS) * L::bytes * kStagedThreads};
+        stage_issue<P, RECON, J + NS - 1>(A, c, cb, in, lo, li, nx, tid);
+    }
+    cp_async_commit();
+    cp_async_wait<NS - 1>();
+    Stage<P, RECON> cur{smem + (J % NS) * L::bytes * kStagedThreads};
+    stage_compute<P, RECON, J, DAGGER>(A, c, cur, tid, acc, bs);
+    if constexpr (J < 7) staged_step<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid, acc, bs);
+}
+
+template <int P, int RECON, bool DAGGER, int NS, int J>
+__device__ __forceinline__ void staged_prologue(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                                const char *lo, const char *li, char *smem, int T, int tid) {
+    using L = HopLayout<P, RECON>;
+    if constexpr (J < NS - 1) {
+        Stage<P, RECON> st{smem + J * L::bytes * kStagedThreads};
+        stage_issue<P, RECON, J>(A, c, cb, in, lo, li, st, tid);
+        cp_async_commit();
+        staged_prologue<P, RECON, DAGGER, NS, J + 1>(A, c, cb, in, lo, li, smem, T, tid);
+    }
+}
+
+template <int P, int RECON, bool DAGGER, int NS>
+__device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, int cb, const char *in,
+                                            const char *lo, const char *li, Cx<float> (&acc)[12], float bs) {
+    extern __shared__ __align__(16) char smem_dyn[];
+    constexpr int T = kStagedThreads;  // blockDim.x * blockDim.y, enforced by launch_dslash
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    staged_prologue<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid);
+    staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc, bs);
+}
+
+// Grid: x over (site block, right-hand-side group) pairs of every lattice of
+// the batch, group fastest (lattice l owns [block0, block0 + nblocks *
+// ngroups)), so that the blocks reading the same links run back to back and
+// find them in L1/L2; z over the output parities (1 or 2).
+// Block: (sites, right-hand sides).
+// Register budget: FP16/FP32 at two 256-thread blocks per SM (128 registers,
+// no spills); FP64 is bound by the FP64 pipe and keeps its full register set.
+// The staged kernels always run 128-thread blocks.
+#ifndef COLA_STAGED_MINB
+#define COLA_STAGED_MINB 5
+#endif
+template <int P, int NS>
+struct LaunchShape {
+    static constexpr int threads = NS > 0 ? 128 : 256;
+    static constexpr int min_blocks = P == COLA_F64 ? 1 : NS > 0 ? COLA_STAGED_MINB : COLA_DSLASH_MINB;
+};
+
+template <int P, int RECON, bool DAGGER, int EPI, int NS>
+__global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS>::min_blocks)
+    dslash_kernel(const __grid_constant__ DslashArgs A) {
+    using R = typename Prec<P>::real;
+    int l = 0;
+    while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
+    const DslashLat &L = A.lat[l];
+    const Geom &g = L.g;
+    const int rel = (int)blockIdx.x - L.block0;
+    const int grp = A.ngroups == 1 ? 0 : rel % A.ngroups;
+    const int sblk = A.ngroups == 1 ? rel : rel / A.ngroups;
+    const int cb = sblk * blockDim.x + threadIdx.x;
+    const int rhs = grp * blockDim.y + threadIdx.y;
+    const int row = L.row0 + rhs;
+    const int par = A.parity0 + blockIdx.z;
+    const bool row_ok = rhs < A.nrhs;
+    bool live = row_ok;
+    if (live && A.state) {
+        const CgState &st = A.state[row];
+        live = A.filter_ru ? (st.ru && !st.done) : !st.done;
+    }
+    const bool have = cb < g.Vh && live;
+    Cx<R> acc[12];
+    if (have) {
+        const Coord c = cb_coord(g, cb, par);
+        const char *in = static_cast<const char *>(L.in) + rhs * L.rhs_stride + (1 - par) * L.parity_stride;
+        const char *lo = static_cast<const char *>(L.links) + par * L.link_parity_stride;
+        const char *li = static_cast<const char *>(L.links) + (1 - par) * L.link_parity_stride;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+        if constexpr (NS > 0 && P != COLA_F64) {
+            hops_staged<P, RECON, DAGGER, NS>(L, c, cb, in, lo, li, acc, (float)L.b);
+        } else {
+            hop_mu<P, RECON, 0, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 1, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 2, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+            hop_mu<P, RECON, 3, DAGGER>(L, c, cb, in, lo, li, acc, (R)L.b);
+        }
+        // the factor b is already in every hop's scale
+        if constexpr (EPI == EPI_XPAY || EPI == EPI_CLOVER_X) {
+            const R a = (R)L.a;
+            Cx<R> xs[12];
+            SpinorIO<P>::load(static_cast<const char *>(L.xin) + rhs * L.rhs_stride + par * L.parity_stride,
+                              g.Vh, cb, xs);
+            if constexpr (EPI == EPI_CLOVER_X)
+                clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, xs);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                acc[k].re = fma(a, xs[k].re, acc[k].re);
+                acc[k].im = fma(a, xs[k].im, acc[k].im);
+            }
+        }
+        if constexpr (EPI == EPI_CLOVER_INV)
+            clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, acc);
+    }
+    if (have)
+        SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb, acc);
+}
+
+// Pipeline depth of the staged kernels: FP16 storage moves half the bytes
+// per load of FP32, so it needs the deeper pipeline; FP32 keeps direct loads
+// (measured on GB300 at 32^3x64).  COLA_DSLASH_STAGES=0 or 3 overrides.
+static inline int staged_depth(int prec) {
+    static const int env_ns = [] {
+        const char *e = getenv("COLA_DSLASH_STAGES");
+        return e ? atoi(e) : -1;
+    }();
+    if (prec == COLA_F64) return 0;
+    if (env_ns >= 0) return env_ns == 0 ? 0 : 3;
+    return prec == COLA_F16 ? 3 : 0;
+}
+
+template <int P, int RECON, bool DAGGER, int EPI, int NS>
+static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total_blocks, cudaStream_t s) {
+    const int by = A.rhs_per_block;
+    dim3 block(bx, by, 1);
+    dim3 grid(total_blocks, 1, nparity);
+    size_t smem = 0;
+    if constexpr (NS > 0 && P != COLA_F64) {
+        smem = (size_t)NS * HopLayout<P, RECON>::bytes * bx * by;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(dslash_kernel<P, RECON, DAGGER, EPI, NS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr_set = true;
+        }
+    }
+    dslash_kernel<P, RECON, DAGGER, EPI, NS><<<grid, block, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int P, int RECON, bool DAGGER, int EPI>
+static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cudaStream_t s) {
+    if constexpr (P == COLA_F64) {
+        return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
+    } else {
+        if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, EPI, 3>(A, nparity, bx, nb, s);
+    }
+}
+
+// Launch with epilogue E0 or E1 (epi selects), both daggers.
+template <int P, int RECON, int E0, int E1>
+static cudaError_t launch_r(const DslashArgs &A, int nparity, bool dagger, int epi, int bx, int nb, cudaStream_t s) {
+    if (dagger) return epi == E1 ? launch_t<P, RECON, true, E1>(A, nparity, bx, nb, s)
+                                 : launch_t<P, RECON, true, E0>(A, nparity, bx, nb, s);
+    return epi == E1 ? launch_t<P, RECON, false, E1>(A, nparity, bx, nb, s)
+                     : launch_t<P, RECON, false, E0>(A, nparity, bx, nb, s);
+}
+
+template <int E0, int E1>
+static cudaError_t launch_pr(int prec, int recon, const DslashArgs &A, int nparity, bool dagger, int epi, int bx,
+                             int nb, cudaStream_t s) {
+    switch (prec) {
+        case COLA_F64:
+            return recon == 12 ? launch_r<COLA_F64, 12, E0, E1>(A, nparity, dagger, epi, bx, nb, s)
+                               : launch_r<COLA_F64, 18, E0, E1>(A, nparity, dagger, epi, bx, nb, s);
+        case COLA_F32:
+            return recon == 12 ? launch_r<COLA_F32, 12, E0, E1>(A, nparity, dagger, epi, bx, nb, s)
+                               : launch_r<COLA_F32, 18, E0, E1>(A, nparity, dagger, epi, bx, nb, s);
+        default:
+            return recon == 12 ? launch_r<COLA_F16, 12, E0, E1>(A, nparity, dagger, epi, bx, nb, s)
+                               : launch_r<COLA_F16, 18, E0, E1>(A, nparity, dagger, epi, bx, nb, s);
+    }
+}
+
+}  // namespace cola

@@ -196,6 +196,9 @@ std::vector<unsigned char> graph_key(const SolveCtx &c) {
         put(&g->lat, sizeof(cola_lattice));
         put(g->links, sizeof(g->links));
         put(g->recon, sizeof(g->recon));
+        put(&g->csw, sizeof(double));
+        put(g->clover, sizeof(g->clover));
+        put(g->clover_inv, sizeof(g->clover_inv));
     }
     return k;
 }
@@ -341,6 +344,10 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
     c.nrhs = prm->nrhs;
     c.nparity = prm->op == COLA_OP_EO ? 1 : 2;
     const bool dirac = prm->system == COLA_SYS_DIRAC;
+    // D = A - kappa H with a clover term: every lattice of a batch has one, or none has
+    const bool clv = gs[0]->csw != 0.0;
+    const int epi_x = clv ? EPI_CLOVER_X : EPI_XPAY;
+    const int epi_h = clv ? EPI_CLOVER_INV : EPI_HOP;
     int maxblocks = 0, nrows = nlat * c.nrhs;
     for (int l = 0; l < nlat; ++l) {
         cola_gauge g = gs[l];
@@ -356,6 +363,8 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
             return arg_error("the gauge handles of a batch must use the same link reconstruction per precision");
         for (int m = 0; m < l; ++m)
             if (gs[m] == g) return arg_error("a gauge handle appears twice in the batch (use nrhs instead)");
+        if ((g->csw != 0.0) != clv)
+            return arg_error("either every gauge handle of a batch has a clover term or none has");
         const Geom &G = g->geom;
         LatCtx &L = c.lat[l];
         L.g = g;
@@ -395,16 +404,26 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         } else {
             COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.borig, bs[l], c.nrhs, 3, s), "pack b");
             if (prm->op == COLA_OP_EO) {
-                // bhat_e = b_e + kappa H_eo b_o (into mp64);  b = Mhat^dag bhat
-                DslashArgs A = make_dslash_args(g, COLA_F64, L.mp64, L.borig, L.borig, c.nrhs, 0, 1.0, k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, s));
+                // bhat_e = b_e + kappa H_eo A_oo^-1 b_o (into mp64);  b = Mhat^dag bhat
+                // (without a clover term A = 1)
+                const void *bo = L.borig;
+                if (clv) {
+                    COLA_CUDA(launch_clover_apply(COLA_F64, G, g->clover_inv[COLA_F64], L.t64, L.borig, c.nrhs, 2, s),
+                              "A_oo^-1 b_o");
+                    bo = L.t64;
+                }
+                DslashArgs A = make_dslash_args(g, COLA_F64, L.mp64, bo, L.borig, c.nrhs, 0, 1.0, k);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, EPI_XPAY, s));
                 A = make_dslash_args(g, COLA_F64, L.t64, L.mp64, nullptr, c.nrhs, 1, 0.0, 1.0);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, false, s));
+                if (clv) set_clover(A.lat[0], g, COLA_F64, true);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, epi_h, s));
                 A = make_dslash_args(g, COLA_F64, L.b, L.t64, L.mp64, c.nrhs, 0, 1.0, -k * k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, true, s));
+                if (clv) set_clover(A.lat[0], g, COLA_F64, false);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 1, true, epi_x, s));
             } else {
                 DslashArgs A = make_dslash_args(g, COLA_F64, L.b, L.borig, L.borig, c.nrhs, 0, 1.0, -k);
-                COLA_TRY(dslash_launch(g, COLA_F64, A, 2, true, true, s));
+                if (clv) set_clover(A.lat[0], g, COLA_F64, false);
+                COLA_TRY(dslash_launch(g, COLA_F64, A, 2, true, epi_x, s));
             }
         }
         COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.xhi, xs[l], c.nrhs, prm->op == COLA_OP_EO ? 1 : 3, s), "pack x0");
@@ -484,9 +503,12 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         const Geom &G = g->geom;
         const double k = g->lat.kappa;
         if (dirac && prm->op == COLA_OP_EO) {
-            // x_o = b_o + kappa H_oe x_e
-            DslashArgs A = make_dslash_args(g, COLA_F64, L.xhi, L.xhi, L.borig, c.nrhs, 1, 1.0, k);
-            COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, true, s));
+            // x_o = A_oo^-1 (b_o + kappa H_oe x_e)   (A = 1 without a clover term)
+            DslashArgs A = make_dslash_args(g, COLA_F64, clv ? L.t64 : L.xhi, L.xhi, L.borig, c.nrhs, 1, 1.0, k);
+            COLA_TRY(dslash_launch(g, COLA_F64, A, 1, false, EPI_XPAY, s));
+            if (clv)
+                COLA_CUDA(launch_clover_apply(COLA_F64, G, g->clover_inv[COLA_F64], L.xhi, L.t64, c.nrhs, 2, s),
+                          "x_o = A_oo^-1 (...)");
         }
         if (prm->op == COLA_OP_EO && !dirac) {
             const size_t pb = spinor_parity_bytes(COLA_F64, G.Vh);
@@ -500,7 +522,8 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         for (int l = 0; l < nlat; ++l) {
             LatCtx &L = c.lat[l];
             DslashArgs A = make_dslash_args(L.g, COLA_F64, L.ax, L.xhi, L.xhi, c.nrhs, 0, 1.0, -L.g->lat.kappa);
-            COLA_TRY(dslash_launch(L.g, COLA_F64, A, 2, false, true, s));
+            if (clv) set_clover(A.lat[0], L.g, COLA_F64, false);
+            COLA_TRY(dslash_launch(L.g, COLA_F64, A, 2, false, epi_x, s));
         }
         double *d_norms;
         COLA_TRY(ws_slot(c.owner, S_NORMS, 2 * nrows * sizeof(double), reinterpret_cast<void **>(&d_norms)));

@@ -101,6 +101,10 @@ def test_argument_errors_before_any_cuda_call(lib):
                                  ctypes.byref(h)) == -1
     assert lib.cola_cg_solve(None, None, None, None, None, None) == -1
     assert lib.cola_dslash_apply(None, None, None, None, 0.0, 1.0, 0, 0, 0, 1, None) == -1
+    assert lib.cola_dirac_apply(None, None, None, 0, 0, 1, None) == -1
+    assert lib.cola_clover_attach(None, 1.0, None) == -1
+    assert lib.cola_clover_apply(None, None, None, 2, 0, 0, 1, None) == -1
+    assert lib.cola_clover_csw(None) == 0.0
     assert lib.cola_gauge_destroy(None) == 0
 
 

@@ -280,3 +280,13 @@ def test_tree_level_clover_cancels_the_wilson_shift_of_landau_zero_modes():
     want = kappa * np.abs(np.array([B[0]] * 4 + [B[2]] * 4))
     assert np.max(np.abs(lift - want) / want) < 0.1
     assert np.max(np.abs(low[1.0])) < 0.05 * np.min(lift)
+
+
+def test_clover_sites_matches_whole_lattice():
+    dims = (4, 6, 2, 4)
+    kappa, csw = 0.13, 1.4
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(96, 13))
+    full = clv.clover_matrix(u, kappa, csw).reshape(-1, 4, 3, 4, 3)
+    sites = np.arange(0, full.shape[0], 5)
+    got = clv.clover_sites(u, kappa, csw, sites)
+    assert np.max(np.abs(got - full[sites])) < 1e-14
