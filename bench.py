@@ -312,6 +312,7 @@ def run_cola(args):
     del g32, p32, t32
 
     multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
+    clover = None if args.skip_clover else clover_measurements(cola, dev, u, b)
 
     # end to end through the public API with host buffers: every step copies
     # the canonical links and the source from pinned host memory, re-packs the
@@ -398,6 +399,7 @@ def run_cola(args):
                     "d2h_bytes_per_step": x_host[0].numel() * 16, "ms_per_step": e2e_s * 1e3,
                     "overlap": "copies double-buffered on a copy stream, overlapping the previous and next solve"},
             "multi_rhs": multi,
+            "clover": clover,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -474,6 +476,79 @@ def multi_rhs_measurements(cola, dev):
     return out
 
 
+CSW = 1.0
+# algorithmic bytes per even site of one FP16 even-odd normal-operator apply
+# (4 parity launches): hopping reads and writes as above, the xpay input of the
+# two even-parity launches, and one 6x6-block pair of A or A^-1 (72 halves =
+# 144 B) per output site in each launch with a clover term
+BYTES_MDAGM_F16_WILSON = 2 * BYTES_PER_SITE_F16 + 2 * (BYTES_PER_SITE_F16 + 52)
+BYTES_MDAGM_F16_CLOVER = BYTES_MDAGM_F16_WILSON + 4 * 144
+
+
+def clover_measurements(cola, dev, u, b):
+    """Clover-improved operator on the benchmark's lattice (not part of the timed step).
+
+    c_sw = 1 on the same links and source: the construction of A and A^-1
+    (FP64, once per gauge field), the FP16 even-odd normal operator
+    Mhat^dag Mhat (4 hopping launches with clover epilogues) next to the
+    Wilson one, and the mixed FP16 solve of the same normal system next to
+    plain FP64 CG.  The operator is applied repeatedly to one input (its 55 MB
+    FP16 spinor may stay in L2; links and clover fields, 503 MB, do not).
+    """
+    import torch
+
+    vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f16"), recon={"f64": 18, "f16": 12})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.attach_clover(CSW)
+    build_ms = (time.perf_counter() - t0) * 1e3
+
+    def op_us(gg, reps=50):
+        p16 = cola.pack(gg, b, "f16")
+        q16 = gg.empty_packed("f16")
+        for _ in range(3):
+            cola.mdagm(gg, q16, p16, op="eo", prec="f16")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cola.mdagm(gg, q16, p16, op="eo", prec="f16")
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    us_clover = op_us(g)
+    gw = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f16",), recon={"f16": 12})
+    us_wilson = op_us(gw)
+    del gw
+
+    def solve(inner):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, info = cola.cg_solve(g, b, tol=TOL, op="eo", inner=inner, delta=DELTA, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), info[0]
+
+    solve("f16")
+    ms16, i16 = solve("f16")
+    ms64, i64 = solve("f64")
+    peak, _ = measured_peak_hbm()
+    gbs = BYTES_MDAGM_F16_CLOVER * vh / (us_clover * 1e-6) / 1e9
+    return {
+        "csw": CSW, "construction_ms": build_ms,
+        "mdagm_eo_f16": {"us_clover": us_clover, "us_wilson": us_wilson, "clover_over_wilson": us_clover / us_wilson,
+                         "algorithmic_gbs": gbs, "hbm_frac": gbs / peak,
+                         "bytes_per_even_site": BYTES_MDAGM_F16_CLOVER},
+        "mixed_f16_solve": {"ms": ms16, "iters": i16.iters, "reliable_updates": i16.reliable_updates,
+                            "true_rel_resid": i16.true_rel_resid},
+        "fp64_cg": {"ms": ms64, "iters": i64.iters, "true_rel_resid": i64.true_rel_resid,
+                    "mixed_over_fp64_time": ms16 / ms64},
+    }
+
+
 def run_dslash_only(args):
     """Chained parity Dslash applies only (the case profiled with ncu)."""
     import torch
@@ -483,15 +558,23 @@ def run_dslash_only(args):
     torch.cuda.set_device(0)
     u, b = make_inputs(torch.device("cuda", 0))
     prec = args.prec
-    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
+    if args.clover:
+        # the even-odd normal operator with clover epilogues (4 launches per apply)
+        g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", prec), recon={"f64": 18, prec: args.recon})
+        g.attach_clover(CSW)
+    else:
+        g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
     del u
     p = cola.pack(g, b, prec)
     t = g.empty_packed(prec)
     for _ in range(args.reps):
-        cola.dslash(g, t, p, parity=1, prec=prec)
-        cola.dslash(g, p, t, parity=0, prec=prec)
+        if args.clover:
+            cola.mdagm(g, t, p, op="eo", prec=prec)
+        else:
+            cola.dslash(g, t, p, parity=1, prec=prec)
+            cola.dslash(g, p, t, parity=0, prec=prec)
     torch.cuda.synchronize()
-    print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps}))
+    print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps, "clover": bool(args.clover)}))
 
 
 def run_solve_only(args):
@@ -521,6 +604,7 @@ def main():
     ap.add_argument("--lattice", default="24x24x24x48")
     ap.add_argument("--dslash-only", action="store_true", help="run chained parity Dslash applies and exit")
     ap.add_argument("--prec", default="f16")
+    ap.add_argument("--clover", action="store_true", help="with --dslash-only: the clover normal operator")
     ap.add_argument("--recon", type=int, default=12)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,6 +613,7 @@ def main():
     ap.add_argument("--impl", default="cola", choices=["cola", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-multi-rhs", action="store_true", help="skip the multi-RHS and batched solves")
+    ap.add_argument("--skip-clover", action="store_true", help="skip the clover-operator measurements")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loop from the host instead of one conditional CUDA graph (ncu cannot "
                          "profile kernels inside graphs with conditional nodes)")
