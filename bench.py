@@ -556,11 +556,22 @@ def run_dslash_only(args):
     import paper_2302_00850_gb300 as cola
 
     torch.cuda.set_device(0)
-    u, b = make_inputs(torch.device("cuda", 0))
+    dims = DIMS
+    if args.clover:
+        import synth
+
+        # a smaller lattice keeps the FP64 links and clover fields of the
+        # profiled process to about 1.5 GB (still well above L2)
+        dims = tuple(int(v) for v in args.lattice.split("x"))
+        dev = torch.device("cuda", 0)
+        u = synth.gauge_field(dims, EPS, synth.seed_for(CONFIG_ID, 0), device=dev, as_numpy=False)
+        b = torch.from_numpy(synth.gaussian_spinor(dims, synth.seed_for(CONFIG_ID, 1))).to(dev)
+    else:
+        u, b = make_inputs(torch.device("cuda", 0))
     prec = args.prec
     if args.clover:
         # the even-odd normal operator with clover epilogues (4 launches per apply)
-        g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", prec), recon={"f64": 18, prec: args.recon})
+        g = cola.Gauge(u, dims, KAPPA, BC, precisions=("f64", prec), recon={"f64": 18, prec: args.recon})
         g.attach_clover(CSW)
     else:
         g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
@@ -574,7 +585,8 @@ def run_dslash_only(args):
             cola.dslash(g, t, p, parity=1, prec=prec)
             cola.dslash(g, p, t, parity=0, prec=prec)
     torch.cuda.synchronize()
-    print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps, "clover": bool(args.clover)}))
+    print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps, "clover": bool(args.clover),
+                      "lattice": "x".join(map(str, dims))}))
 
 
 def run_solve_only(args):
