@@ -20,6 +20,8 @@ definitions, each stated where it is coded:
   force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
   clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H
              and its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe
+  hmc.py     Wilson gauge action and force, momenta, leapfrog and Omelyan
+             integrators, the Hamiltonian and the Metropolis step
 
 Pins (tests/test_oracle_*.py, run without a GPU): gamma algebra; the free
 field closed form (plane waves and the full D^dag D spectrum); gamma5
@@ -30,8 +32,10 @@ an exactly computed action and against the closed form S = |eta|^2 at
 phi = D^dag eta; for the clover term the unit-gauge reduction, a constant
 abelian field in closed form, the weak-field lattice curl, gauge covariance,
 dense Schur identities and the tree-level cancellation of the Wilson lift of
-Landau zero modes (which fixes its sign).  Every function here is pinned by
-at least one of them.
+Landau zero modes (which fixes its sign); for HMC the gauge force against
+finite differences of the action, exact free motion, reversibility and the
+second-order scaling of dH.  Every function here is pinned by at least one
+of them.
 """
 from .wilson import (  # noqa: F401
     GAMMA, GAMMA5, IDENTITY4, parity_of_sites, even_mask, phased_links, hop,

@@ -1,0 +1,119 @@
+"""Pins of the oracle's HMC (CPU only).
+
+- the gauge action: zero at U = 1, gauge invariant, and a hand-built constant
+  abelian field in closed form (beta V (1 - mean cos B_c) in the flux plane);
+- the gauge force against central finite differences of the action, along a
+  random su(3) direction and along single (link, generator) pairs;
+- free motion (beta = 0, no fermions) is U(tau) = exp(i tau P) U exactly;
+- reversibility: integrating back with -p returns the start (leapfrog and
+  Omelyan, with and without fermions);
+- energy conservation: dH falls by about 4 when the step halves (both
+  integrators are second order), and Omelyan's dH is below leapfrog's;
+- the start of a trajectory: S_F = |eta|^2 at phi = D^dag eta.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.hmc as hmc
+import synth
+from test_oracle_clover import _abelian_field
+
+BC_AP = (1.0, 1.0, 1.0, -1.0)
+
+
+def momenta(dims, seed):
+    return synth.su3_direction(dims, synth.seed_for(97, seed))
+
+
+def test_gauge_action_zero_at_unit_and_gauge_invariant():
+    dims = (4, 2, 4, 2)
+    assert hmc.gauge_action(synth.unit_gauge(dims), 5.5) == 0.0
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(97, 0))
+    om = synth.random_su3_field(dims, synth.seed_for(97, 1), eps=1.0)
+    ug = np.empty_like(u)
+    for mu in range(4):
+        ug[mu] = np.einsum("...ab,...bc,...dc->...ad", om, u[mu], np.roll(om, -1, axis=3 - mu).conj())
+    assert abs(hmc.gauge_action(ug, 5.5) - hmc.gauge_action(u, 5.5)) < 1e-12 * hmc.gauge_action(u, 5.5)
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (2, 3)])
+def test_gauge_action_constant_abelian_field(plane):
+    dims = (4, 6, 2, 4)
+    u, B = _abelian_field(dims, plane[0], plane[1], (1, 2, -3))
+    vol = int(np.prod(dims))
+    want = 5.5 * vol * (1.0 - np.mean(np.cos(B)))
+    assert abs(hmc.gauge_action(u, 5.5) - want) < 1e-12 * want
+
+
+def test_gauge_force_finite_differences():
+    dims = (2, 4, 2, 4)
+    beta = 5.7
+    u = synth.gauge_field(dims, 0.4, synth.seed_for(97, 2))
+    f = hmc.gauge_force(u, beta)
+    omega = momenta(dims, 3)
+    h = 1e-5
+    fd = (hmc.gauge_action(oracle.link_variation(u, omega, h), beta)
+          - hmc.gauge_action(oracle.link_variation(u, omega, -h), beta)) / (2 * h)
+    assert abs(fd - np.sum(f * omega)) < 1e-7 * np.sum(np.abs(f * omega))
+    for (mu, site, a) in [(0, (0, 0, 0, 0), 0), (3, (3, 1, 2, 1), 7), (1, (1, 0, 3, 1), 4)]:
+        e = np.zeros_like(omega)
+        e[(mu,) + site + (a,)] = 1.0
+        fd = (hmc.gauge_action(oracle.link_variation(u, e, h), beta)
+              - hmc.gauge_action(oracle.link_variation(u, e, -h), beta)) / (2 * h)
+        assert abs(fd - f[(mu,) + site + (a,)]) < 1e-8
+
+
+def test_free_motion_is_exact():
+    dims = (2, 2, 2, 4)
+    u = synth.gauge_field(dims, 0.4, synth.seed_for(97, 4))
+    p = momenta(dims, 5)
+    u1, p1 = hmc.integrate(u, p, None, 0.0, 0.0, BC_AP, 0.7, 5, "leapfrog")
+    assert np.array_equal(p1, p)
+    assert np.max(np.abs(u1 - oracle.link_variation(u, p, 0.7))) < 1e-13
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+@pytest.mark.parametrize("fermions", [False, True])
+def test_reversibility(integrator, fermions):
+    dims = (2, 2, 2, 4)
+    kappa, beta = 0.12, 5.6
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(97, 6))
+    p = momenta(dims, 7)
+    phi = synth.gaussian_spinor(dims, synth.seed_for(97, 8)) if fermions else None
+    u1, p1 = hmc.integrate(u, p, phi, beta, kappa, BC_AP, 0.4, 4, integrator, tol=1e-13)
+    u0, p0 = hmc.integrate(u1, -p1, phi, beta, kappa, BC_AP, 0.4, 4, integrator, tol=1e-13)
+    assert np.max(np.abs(u0 - u)) < 1e-10
+    assert np.max(np.abs(-p0 - p)) < 1e-9
+    assert np.max(np.abs(u1 - u)) > 1e-2
+
+
+def test_energy_conservation_is_second_order():
+    dims = (2, 2, 2, 4)
+    kappa, beta = 0.12, 5.6
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(97, 9))
+    p = momenta(dims, 10)
+    eta = synth.gaussian_spinor(dims, synth.seed_for(97, 11))
+    dh = {}
+    for integrator in ("leapfrog", "omelyan"):
+        for n in (4, 8):
+            _, dh[integrator, n], _ = hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.5, n, integrator,
+                                                     tol=1e-13)
+        r = dh[integrator, 4] / dh[integrator, 8]
+        assert 3.0 < r < 5.0, (integrator, r, dh)
+    assert abs(dh["omelyan", 4]) < abs(dh["leapfrog", 4])
+
+
+def test_trajectory_start_and_metropolis():
+    dims = (2, 2, 2, 2)
+    kappa, beta = 0.12, 5.6
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(97, 12))
+    eta = synth.gaussian_spinor(dims, synth.seed_for(97, 13))
+    phi = oracle.dirac_dag(u, eta, kappa, BC_AP)
+    assert abs(hmc.fermion_action(u, phi, kappa, BC_AP) - np.sum(np.abs(eta) ** 2)) < 1e-10 * np.sum(np.abs(eta) ** 2)
+    p = momenta(dims, 14)
+    u_acc, dh, acc = hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.3, 3, uniform=0.0)
+    assert acc and not np.array_equal(u_acc, u)
+    u_rej, dh2, acc2 = hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.3, 3, uniform=1.0 - 1e-300)
+    assert dh2 == dh
+    assert acc2 == (dh < 0) and (acc2 or np.array_equal(u_rej, u))
