@@ -230,6 +230,70 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
 cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev,
                                  const void *gy_dev, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- HMC ----
+ * Hybrid Monte Carlo around the fermion force (HMC is one of COLA's key
+ * algorithms in the paper's overview; the formulas are the standard ones).
+ * Links without fermion boundary phases enter the Wilson gauge action
+ *   S_G = beta sum_x sum_{mu<nu} (1 - Re tr U_munu(x) / 3),
+ *   U_munu(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag.
+ * Momenta and forces are real FP64 [4][V][8] coefficients of the generators
+ * T^a = lambda^a / 2 (Gell-Mann); P_mu(x) = sum_a p^a T^a, kinetic energy
+ * K = sum p^2 / 2; a force is dS/deps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x),
+ * as for cola_fermion_force.  Pseudofermions: phi = D^dag eta,
+ * S_F = phi^dag (D^dag D)^-1 phi (whole-lattice D, FP64 Wilson).  H = K + S_G + S_F. */
+
+/* Mean plaquette (1/6V) sum Re tr U_munu / 3 of the handle's FP64 links,
+ * written to *plaq (host); waits for the stream. */
+cola_status cola_plaquette(cola_gauge g, double *plaq, cudaStream_t stream);
+
+/* force_dev = dS_G/deps^a (FP64 [4][V][8], device). */
+cola_status cola_gauge_force(cola_gauge g, double beta, double *force_dev, cudaStream_t stream);
+
+/* links_dev (canonical FP64 [4][V][3][3], device, the field the handle was
+ * created or last updated from) <- exp(i eps P) U link by link, then the
+ * handle is re-packed from it (and its clover term rebuilt) as by
+ * cola_gauge_update.  The exponential is a scaled Taylor series in FP64. */
+cola_status cola_link_update(cola_gauge g, void *links_dev, const double *mom_dev, double eps,
+                             cudaStream_t stream);
+
+enum { COLA_INT_LEAPFROG = 0, COLA_INT_OMELYAN = 1 };
+
+typedef struct {
+    double beta;            /* gauge coupling */
+    double tau;             /* trajectory length */
+    int nsteps;             /* integration steps (step eps = tau / nsteps) */
+    int integrator;         /* COLA_INT_LEAPFROG, or COLA_INT_OMELYAN (2MN, lambda = 0.1931833275037836) */
+    double uniform;         /* Metropolis random number in [0, 1): accept if uniform < exp(-dH) */
+    cola_solver_params md;  /* force solves of D^dag D (op and system are set to FULL and NORMAL) */
+    double action_tol;      /* tolerance of the final action solve */
+} cola_hmc_params;
+
+typedef struct {
+    double dH, H0, H1;  /* H1 - H0, start and end Hamiltonians */
+    int accepted;
+    double plaquette;   /* mean plaquette of the links on return */
+    int force_evals;    /* force evaluations of the trajectory */
+    int cg_iters;       /* CG iterations summed over every solve */
+    double seconds;
+} cola_hmc_info;
+
+/* One HMC update of the gauge field links_dev (canonical FP64, device, in
+ * and out; the handle must be created from or last updated with it, hold
+ * FP64 links and have no clover term) with momenta mom_dev (FP64 [4][V][8],
+ * device, drawn by the caller from N(0, 1); on return the final momenta of
+ * the trajectory) and pseudofermion source eta_dev (canonical spinor,
+ * device, drawn by the caller; NULL for the pure gauge theory).
+ * phi = D^dag eta; H0 = K + S_G + |eta|^2; the molecular-dynamics trajectory
+ * (leapfrog: p -= eps/2 F; n x [U <- exp(i eps P) U; p -= eps F], the last
+ * momentum step eps/2; Omelyan 2MN: p -= lam eps F; U <- exp(i eps/2 P) U;
+ * p -= (1 - 2 lam) eps F; U <- exp(i eps/2 P) U; p -= lam eps F, the two
+ * adjacent lam steps of consecutive steps merged), F = dS_G/deps +
+ * dS_F/deps with X = (D^dag D)^-1 phi solved from a zero guess; then H1 and
+ * the Metropolis test.  On rejection links_dev and the handle are restored
+ * bitwise.  Waits for the stream. */
+cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, const void *eta_dev,
+                                const cola_hmc_params *params, cola_hmc_info *info, cudaStream_t stream);
+
 /* Thread-local message describing the last error returned on this thread. */
 const char *cola_last_error(void);
 

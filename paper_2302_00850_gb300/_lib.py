@@ -49,6 +49,18 @@ class SolveInfo(ctypes.Structure):
                 ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class HmcParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("integrator", ctypes.c_int), ("uniform", ctypes.c_double), ("md", SolverParams),
+                ("action_tol", ctypes.c_double)]
+
+
+class HmcInfo(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("plaquette", ctypes.c_double), ("force_evals", ctypes.c_int),
+                ("cg_iters", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
@@ -74,6 +86,10 @@ SIGNATURES = {
                                      ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_fermion_force": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_dirac_link_grad": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cola_plaquette": (_st, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "cola_gauge_force": (_st, [_vp, _d, _vp, _vp]),
+    "cola_link_update": (_st, [_vp, _vp, _vp, _d, _vp]),
+    "cola_hmc_trajectory": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(HmcParams), ctypes.POINTER(HmcInfo), _vp]),
     "cola_last_error": (ctypes.c_char_p, []),
 }
 

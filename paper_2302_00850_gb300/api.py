@@ -264,3 +264,63 @@ def dirac_link_grad(g: Gauge, psi: torch.Tensor, gy: torch.Tensor) -> torch.Tens
     check(g.lib.cola_dirac_link_grad(g.handle, _ptr(out), _complex_field(psi, g.volume * 12, "psi"),
                                      _complex_field(gy, g.volume * 12, "gy"), _stream(g.device)))
     return out
+
+
+# ------------------------------------------------------------------- HMC --
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1}
+
+
+@dataclass
+class HmcInfo:
+    dH: float
+    H0: float
+    H1: float
+    accepted: bool
+    plaquette: float
+    force_evals: int
+    cg_iters: int
+    seconds: float
+
+
+def plaquette(g: Gauge) -> float:
+    """Mean plaquette of the handle's links."""
+    out = ctypes.c_double()
+    check(g.lib.cola_plaquette(g.handle, ctypes.byref(out), _stream(g.device)))
+    return out.value
+
+
+def _mom_field(t: torch.Tensor, g: Gauge) -> int:
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != 4 * g.volume * 8:
+        raise ValueError("momenta/forces must be contiguous float64 CUDA tensors of 4*V*8 elements")
+    return t.data_ptr()
+
+
+def gauge_force(g: Gauge, beta: float) -> torch.Tensor:
+    """dS_G/deps^a of the Wilson gauge action, float64 [4, Lt, Lz, Ly, Lx, 8]."""
+    lx, ly, lz, lt = g.dims
+    out = torch.empty((4, lt, lz, ly, lx, 8), dtype=torch.float64, device=g.device)
+    check(g.lib.cola_gauge_force(g.handle, float(beta), _mom_field(out, g), _stream(g.device)))
+    return out
+
+
+def link_update(g: Gauge, links: torch.Tensor, mom: torch.Tensor, eps: float) -> torch.Tensor:
+    """links <- exp(i eps P) links in place (and the handle re-packed); returns links."""
+    check(g.lib.cola_link_update(g.handle, _complex_field(links, 4 * g.volume * 9, "links"), _mom_field(mom, g),
+                                 float(eps), _stream(g.device)))
+    return links
+
+
+def hmc_trajectory(g: Gauge, links: torch.Tensor, mom: torch.Tensor, eta: torch.Tensor | None, beta: float,
+                   tau: float, nsteps: int, integrator="leapfrog", uniform=0.5, md_tol=1e-10, md_inner="f64",
+                   delta=0.1, action_tol=1e-12, use_graph=True) -> HmcInfo:
+    """One HMC update (see cola_hmc_trajectory); links and mom are updated in place."""
+    md = _lib.SolverParams(float(md_tol), 100000, OPS["full"], SYSTEMS["normal"], PREC[md_inner], float(delta), 1,
+                           int(bool(use_graph)))
+    prm = _lib.HmcParams(float(beta), float(tau), int(nsteps), INTEGRATORS[integrator], float(uniform), md,
+                         float(action_tol))
+    info = _lib.HmcInfo()
+    eta_p = None if eta is None else _complex_field(eta, g.volume * 12, "eta")
+    check(g.lib.cola_hmc_trajectory(g.handle, _complex_field(links, 4 * g.volume * 9, "links"), _mom_field(mom, g),
+                                    eta_p, ctypes.byref(prm), ctypes.byref(info), _stream(g.device)))
+    return HmcInfo(info.dH, info.H0, info.H1, bool(info.accepted), info.plaquette, info.force_evals, info.cg_iters,
+                   info.seconds)

@@ -39,42 +39,6 @@ struct BuildArgs {
     int *bad;
 };
 
-__device__ __forceinline__ int wrap(int x, int l) { return x < 0 ? x + l : x >= l ? x - l : x; }
-
-// U_mu at site X + dm e_mu' + dn e_nu' (periodic), where the offsets have
-// already been added into p[4].
-template <int RECON>
-__device__ __forceinline__ void link_at(const BuildArgs &A, const int (&p)[4], int mu, C64 (&u)[9]) {
-    const Geom &g = A.g;
-    const int x = wrap(p[0], g.L[0]), y = wrap(p[1], g.L[1]), z = wrap(p[2], g.L[2]), t = wrap(p[3], g.L[3]);
-    const int par = (x + y + z + t) & 1;
-    const int cb = (x >> 1) + g.Lxh * (y + g.L[1] * (z + g.L[2] * t));
-    LinkIO<COLA_F64, RECON>::load(A.links + par * A.link_parity_stride + mu * A.link_dir_stride, g.Vh, cb, u);
-}
-
-// w <- w op(u), op = identity or adjoint
-__device__ __forceinline__ void rmul(C64 (&w)[9], const C64 (&u)[9], bool adj) {
-    C64 r[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            C64 s = {0.0, 0.0};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (adj) {  // (u^dag)_kj = conj(u_jk)
-                    const C64 v = {u[3 * j + k].re, -u[3 * j + k].im};
-                    cmac(s, w[3 * i + k], v);
-                } else {
-                    cmac(s, w[3 * i + k], u[3 * k + j]);
-                }
-            }
-            r[3 * i + j] = s;
-        }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) w[k] = r[k];
-}
-
 // One factor of a leaf: the link of direction `d` (0: mu, 1: nu) at offset
 // (om, on) along (mu, nu) from the site, adjoint or not.
 struct Factor {
@@ -120,16 +84,9 @@ __global__ void __launch_bounds__(128) clover_build_kernel(const __grid_constant
                     p[mu] += fa.om;
                     p[nu] += fa.on;
                     C64 u[9];
-                    link_at<RECON>(A, p, fa.d ? nu : mu, u);
-                    if (f == 0) {
-#pragma unroll
-                        for (int i = 0; i < 3; ++i)
-#pragma unroll
-                            for (int j = 0; j < 3; ++j)
-                                w[3 * i + j] = fa.adj ? C64{u[3 * j + i].re, -u[3 * j + i].im} : u[3 * i + j];
-                    } else {
-                        rmul(w, u, fa.adj != 0);
-                    }
+                    link_at<RECON>(g, A.links, A.link_dir_stride, p, fa.d ? nu : mu, u);
+                    if (f == 0) mat3_set(w, u, fa.adj != 0);
+                    else mat3_rmul(w, u, fa.adj != 0);
                 }
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {

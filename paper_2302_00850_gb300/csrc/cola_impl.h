@@ -134,10 +134,26 @@ cudaError_t launch_axpby(BlasArgs &B, cudaStream_t s);
 int blas_max_blocks(const BlasArgs &B);
 
 // ----------------------------------------------------------------- force --
+// force = coef F (accumulate: force += coef F), F the fermion force [4][V][8]
 cudaError_t launch_force(const Geom &g, double kappa, const void *links_f64, int recon, double *force,
-                         const void *X, const void *Y, cudaStream_t s);
+                         const void *X, const void *Y, cudaStream_t s, double coef = 1.0, bool accumulate = false);
 cudaError_t launch_link_grad(const Geom &g, double kappa, void *grad, const void *psi, const void *gy,
                              cudaStream_t s);
+
+// ----------------------------------------------------------------- gauge --
+// out = coef * dS_G/deps (accumulate: out += ...), [4][V][8], from FP64 links
+cudaError_t launch_gauge_force(const Geom &g, const void *links_f64, int recon, double beta, double coef, double *out,
+                               bool accumulate, cudaStream_t s);
+// doubles of reduction scratch the two reductions below need
+size_t gauge_scratch_doubles(const Geom &g);
+// *out = sum over sites and planes mu < nu of Re tr U_munu(x) / 3 (device)
+cudaError_t launch_plaquette_sum(const Geom &g, const void *links_f64, int recon, double *scratch, double *out,
+                                 cudaStream_t s);
+// *out = scale * sum_k a[k] b[k] (device), deterministic
+cudaError_t launch_dot(const double *a, const double *b, size_t n, double scale, double *scratch, double *out,
+                       cudaStream_t s);
+// canonical links U_mu(x) <- exp(i eps P_mu(x)) U_mu(x)
+cudaError_t launch_link_update(const Geom &g, void *links_canon, const double *mom, double eps, cudaStream_t s);
 
 // ------------------------------------------------------------------ errors --
 void set_error(const std::string &msg);
@@ -161,6 +177,8 @@ struct cola_gauge_s {
     // workspace slots: each a device buffer reused across calls
     static constexpr int kSlots = 24;
     static constexpr int kSlotCloverFlag = kSlots - 1;  // the construction's pivot flag
+    // HMC: saved links, phi, X, Y, two packed FP64 fields, reduction scratch
+    static constexpr int kSlotHmc = 15;
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     double *partials = nullptr;

@@ -352,6 +352,69 @@ struct LinkIO<COLA_F16, RECON> {
     }
 };
 
+// ------------------------------------------- links by lattice coordinates --
+// Gauge-field kernels (plaquettes, staples, clover leaves) visit links at
+// arbitrary offsets from a site: these read one FP64 link of the packed
+// field at coordinates p (each within one step of the lattice, wrapped
+// periodically), and multiply 3x3 matrices in registers.
+__device__ __forceinline__ int wrap_coord(int x, int l) { return x < 0 ? x + l : x >= l ? x - l : x; }
+
+template <int RECON>
+__device__ __forceinline__ void link_at(const Geom &g, const char *links, size_t link_dir_stride, const int (&p)[4],
+                                        int mu, Cx<double> (&u)[9]) {
+    const int x = wrap_coord(p[0], g.L[0]), y = wrap_coord(p[1], g.L[1]);
+    const int z = wrap_coord(p[2], g.L[2]), t = wrap_coord(p[3], g.L[3]);
+    const int par = (x + y + z + t) & 1;
+    const int cb = (x >> 1) + g.Lxh * (y + g.L[1] * (z + g.L[2] * t));
+    LinkIO<COLA_F64, RECON>::load(links + (size_t)(4 * par + mu) * link_dir_stride, g.Vh, cb, u);
+}
+
+// w = op(u), op = identity or adjoint
+__device__ __forceinline__ void mat3_set(Cx<double> (&w)[9], const Cx<double> (&u)[9], bool adj) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) w[3 * i + j] = adj ? Cx<double>{u[3 * j + i].re, -u[3 * j + i].im} : u[3 * i + j];
+}
+
+// w <- w op(u)
+__device__ __forceinline__ void mat3_rmul(Cx<double> (&w)[9], const Cx<double> (&u)[9], bool adj) {
+    Cx<double> r[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Cx<double> s = {0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (adj) cmac(s, w[3 * i + k], Cx<double>{u[3 * j + k].re, -u[3 * j + k].im});
+                else cmac(s, w[3 * i + k], u[3 * k + j]);
+            }
+            r[3 * i + j] = s;
+        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = r[k];
+}
+
+// f_a = Im Tr[lambda^a w] for the Gell-Mann matrices lambda^1..8
+__device__ __forceinline__ void im_tr_lambda(const Cx<double> (&w)[9], double (&f)[8]) {
+    f[0] = w[3].im + w[1].im;
+    f[1] = w[1].re - w[3].re;
+    f[2] = w[0].im - w[4].im;
+    f[3] = w[6].im + w[2].im;
+    f[4] = w[2].re - w[6].re;
+    f[5] = w[7].im + w[5].im;
+    f[6] = w[5].re - w[7].re;
+    f[7] = (w[0].im + w[4].im - 2.0 * w[8].im) * 0.57735026918962576451;  // 1/sqrt(3)
+}
+
+// out[0..7] = coef f (accumulate: out += coef f); one link's eight
+// generator coefficients of a force or momentum field [4][V][8]
+__device__ __forceinline__ void store_force(double *out, const double (&f)[8], double coef, bool accumulate) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[a] = accumulate ? fma(coef, f[a], out[a]) : coef * f[a];
+}
+
 // ---------------------------------------------------------- clover access --
 // The clover matrix A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_munu F_munu(x)
 // (or its inverse) commutes with gamma5 = diag(1, 1, -1, -1), so it is two

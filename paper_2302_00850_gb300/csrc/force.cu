@@ -79,7 +79,7 @@ __device__ __forceinline__ int site_fwd(const Geom &g, int i, const int (&c)[4],
 
 template <int MU, int RECON>
 __device__ void force_link(const Geom &g, double kappa, const void *links, int i, const int (&c)[4],
-                           const double2 *X, const double2 *Y, double *out) {
+                           const double2 *X, const double2 *Y, double *out, double coef, bool accumulate) {
     const int j = site_fwd(g, i, c, MU);
     Cx<double> xs[12], ys[12];
     Cx<double> hx[2][3], hy[2][3];
@@ -119,31 +119,24 @@ __device__ void force_link(const Geom &g, double kappa, const void *links, int i
             cmac(s, u[3 * a + 2], m[6 + b]);
             w[3 * a + b] = s;
         }
-    // F^a = -kappa Im Tr[lambda^a W]
-    const double k = -kappa;
-    double *f = out + ((size_t)MU * g.V + i) * 8;
-    f[0] = k * (w[3].im + w[1].im);
-    f[1] = k * (w[1].re - w[3].re);
-    f[2] = k * (w[0].im - w[4].im);
-    f[3] = k * (w[6].im + w[2].im);
-    f[4] = k * (w[2].re - w[6].re);
-    f[5] = k * (w[7].im + w[5].im);
-    f[6] = k * (w[5].re - w[7].re);
-    f[7] = k * (w[0].im + w[4].im - 2.0 * w[8].im) * 0.57735026918962576451;  // 1/sqrt(3)
+    // F^a = -kappa Im Tr[lambda^a W], times coef, stored or added
+    double fa[8];
+    im_tr_lambda(w, fa);
+    store_force(out + ((size_t)MU * g.V + i) * 8, fa, -kappa * coef, accumulate);
 }
 
 template <int RECON>
 __global__ void __launch_bounds__(128) force_kernel(const Geom g, double kappa, const void *links, double *out,
-                                                    const double2 *X, const double2 *Y) {
+                                                    const double2 *X, const double2 *Y, double coef, int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
     int c[4];
     site_coords(g, i, c);
     switch (blockIdx.y) {
-        case 0: force_link<0, RECON>(g, kappa, links, i, c, X, Y, out); break;
-        case 1: force_link<1, RECON>(g, kappa, links, i, c, X, Y, out); break;
-        case 2: force_link<2, RECON>(g, kappa, links, i, c, X, Y, out); break;
-        default: force_link<3, RECON>(g, kappa, links, i, c, X, Y, out); break;
+        case 0: force_link<0, RECON>(g, kappa, links, i, c, X, Y, out, coef, accumulate); break;
+        case 1: force_link<1, RECON>(g, kappa, links, i, c, X, Y, out, coef, accumulate); break;
+        case 2: force_link<2, RECON>(g, kappa, links, i, c, X, Y, out, coef, accumulate); break;
+        default: force_link<3, RECON>(g, kappa, links, i, c, X, Y, out, coef, accumulate); break;
     }
 }
 
@@ -194,12 +187,12 @@ __global__ void __launch_bounds__(128) link_grad_kernel(const Geom g, double kap
 }
 
 cudaError_t launch_force(const Geom &g, double kappa, const void *links_f64, int recon, double *force,
-                         const void *X, const void *Y, cudaStream_t s) {
+                         const void *X, const void *Y, cudaStream_t s, double coef, bool accumulate) {
     dim3 block(128), grid((g.V + 127) / 128, 4);
     const double2 *x = static_cast<const double2 *>(X);
     const double2 *y = static_cast<const double2 *>(Y);
-    if (recon == 12) force_kernel<12><<<grid, block, 0, s>>>(g, kappa, links_f64, force, x, y);
-    else force_kernel<18><<<grid, block, 0, s>>>(g, kappa, links_f64, force, x, y);
+    if (recon == 12) force_kernel<12><<<grid, block, 0, s>>>(g, kappa, links_f64, force, x, y, coef, accumulate);
+    else force_kernel<18><<<grid, block, 0, s>>>(g, kappa, links_f64, force, x, y, coef, accumulate);
     return cudaGetLastError();
 }
 

@@ -105,7 +105,25 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.cola_clover_attach(None, 1.0, None) == -1
     assert lib.cola_clover_apply(None, None, None, 2, 0, 0, 1, None) == -1
     assert lib.cola_clover_csw(None) == 0.0
+    assert lib.cola_plaquette(None, None, None) == -1
+    assert lib.cola_gauge_force(None, 5.6, None, None) == -1
+    assert lib.cola_link_update(None, None, None, 0.1, None) == -1
     assert lib.cola_gauge_destroy(None) == 0
+
+
+def test_hmc_parameter_errors_before_any_cuda_call(lib):
+    from paper_2302_00850_gb300 import _lib
+
+    fake = ctypes.c_void_p(1)  # never dereferenced: parameters are checked first
+    info = _lib.HmcInfo()
+    md = _lib.SolverParams(1e-10, 100, 0, 0, 0, 0.1, 1, 0)
+    for kw in [dict(beta=-1.0), dict(tau=0.0), dict(nsteps=0), dict(integrator=2), dict(uniform=1.0),
+               dict(uniform=-0.1), dict(action_tol=0.0)]:
+        p = dict(beta=5.6, tau=1.0, nsteps=4, integrator=0, uniform=0.5, action_tol=1e-12)
+        p.update(kw)
+        prm = _lib.HmcParams(p["beta"], p["tau"], p["nsteps"], p["integrator"], p["uniform"], md, p["action_tol"])
+        assert lib.cola_hmc_trajectory(fake, fake, fake, None, ctypes.byref(prm), ctypes.byref(info), None) == -1, kw
+    assert lib.cola_hmc_trajectory(None, fake, fake, None, None, ctypes.byref(info), None) == -1
 
 
 def test_solver_parameter_errors_before_any_cuda_call(lib):
