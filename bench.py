@@ -313,6 +313,7 @@ def run_cola(args):
 
     multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
     clover = None if args.skip_clover else clover_measurements(cola, dev, u, b)
+    hmc = None if args.skip_hmc else hmc_measurements(cola, dev)
 
     # end to end through the public API with host buffers: every step copies
     # the canonical links and the source from pinned host memory, re-packs the
@@ -400,6 +401,7 @@ def run_cola(args):
                     "overlap": "copies double-buffered on a copy stream, overlapping the previous and next solve"},
             "multi_rhs": multi,
             "clover": clover,
+            "hmc": hmc,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -549,6 +551,69 @@ def clover_measurements(cola, dev, u, b):
     }
 
 
+# FP64 flop per link of the Wilson gauge force: 6 staples of 2 SU(3) products
+# each, the product U V, and the staple sums (3x3 complex product = 27 complex
+# multiply-adds = 216 flop)
+GAUGE_FORCE_FLOP_PER_LINK = 13 * 216 + 5 * 18
+
+
+def hmc_measurements(cola, dev):
+    """One HMC trajectory on 24^3x48 (not part of the timed step).
+
+    kappa 0.124, beta 5.6, links exp(0.3 i H), Gaussian momenta and
+    pseudofermion source, tau = 0.5 in 5 Omelyan steps (11 force
+    evaluations), force solves of D^dag D with FP32 inner iterations and FP64
+    reliable updates to 1e-8, final action to 1e-12; the force solves once
+    by CG on D^dag D and once as two even-odd Dirac-system solves (the same
+    X).  Also the isolated gauge-force and link-update kernels.
+    """
+    import torch
+
+    import synth
+
+    d24 = (24, 24, 24, 48)
+    vol = 24 ** 3 * 48
+    u = synth.gauge_field(d24, 0.3, synth.seed_for(5, 0), device=dev, as_numpy=False)
+    mom = torch.from_numpy(synth.su3_direction(d24, synth.seed_for(5, 1))).to(dev)
+    eta = torch.from_numpy(synth.gaussian_spinor(d24, synth.seed_for(5, 2))).to(dev)
+    g = cola.Gauge(u, d24, 0.124, BC, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
+    torch.cuda.synchronize()
+    u0, mom0 = u.clone(), mom.clone()
+    # force solves by CG on D^dag D, then by two even-odd Dirac-system solves
+    info_full = cola.hmc_trajectory(g, u, mom, eta, 5.6, 0.5, 5, "omelyan", uniform=0.0, md_tol=1e-8,
+                                    md_inner="f32", action_tol=1e-12, md_op="full")
+    u.copy_(u0)
+    mom.copy_(mom0)
+    g.update(u)
+    info = cola.hmc_trajectory(g, u, mom, eta, 5.6, 0.5, 5, "omelyan", uniform=0.0, md_tol=1e-8, md_inner="f32",
+                               action_tol=1e-12, md_op="eo")
+
+    def kernel_us(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    gf_us = kernel_us(lambda: cola.gauge_force(g, 5.6))
+    zero = torch.zeros_like(mom)
+    lu_us = kernel_us(lambda: cola.link_update(g, u, zero, 0.0))
+    gf_tflops = GAUGE_FORCE_FLOP_PER_LINK * 4 * vol / (gf_us * 1e-6) / 1e12
+    return {
+        "lattice": "24x24x24x48", "beta": 5.6, "kappa": 0.124, "tau": 0.5, "steps": 5, "integrator": "omelyan",
+        "md_solves": "eo: D W = g5 phi, D X = g5 W (FP32 inner, FP64 reliable updates, 1e-8)",
+        "trajectory_s": info.seconds, "force_evals": info.force_evals, "cg_iters": info.cg_iters, "dH": info.dH,
+        "accepted": info.accepted, "plaquette": info.plaquette,
+        "full_ddag_d_solves": {"trajectory_s": info_full.seconds, "cg_iters": info_full.cg_iters, "dH": info_full.dH},
+        "gauge_force_us": gf_us, "gauge_force_fp64_tflops": gf_tflops, "gauge_force_frac_fp64": gf_tflops / FP64_PEAK_TFLOPS,
+        "link_update_and_repack_us": lu_us,
+    }
+
+
 def run_dslash_only(args):
     """Chained parity Dslash applies only (the case profiled with ncu)."""
     import torch
@@ -589,6 +654,26 @@ def run_dslash_only(args):
                       "lattice": "x".join(map(str, dims))}))
 
 
+def run_gauge_only(args):
+    """Gauge force and link update kernels only on --lattice (the case profiled with ncu)."""
+    import torch
+
+    import paper_2302_00850_gb300 as cola
+    import synth
+
+    torch.cuda.set_device(0)
+    dims = tuple(int(v) for v in args.lattice.split("x"))
+    dev = torch.device("cuda", 0)
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(5, 0), device=dev, as_numpy=False)
+    mom = torch.from_numpy(synth.su3_direction(dims, synth.seed_for(5, 1))).to(dev)
+    g = cola.Gauge(u, dims, 0.124, BC, precisions=("f64",), recon={"f64": 18})
+    for _ in range(args.reps):
+        cola.gauge_force(g, 5.6)
+        cola.link_update(g, u, mom, 0.01)
+    torch.cuda.synchronize()
+    print(json.dumps({"gauge_only": args.lattice, "reps": args.reps}))
+
+
 def run_solve_only(args):
     """One mixed-precision even-odd solve on a smaller lattice (the case profiled with ncu)."""
     import torch
@@ -615,6 +700,7 @@ def main():
     ap.add_argument("--solve-only", action="store_true", help="run host-loop solves on --lattice and exit")
     ap.add_argument("--lattice", default="24x24x24x48")
     ap.add_argument("--dslash-only", action="store_true", help="run chained parity Dslash applies and exit")
+    ap.add_argument("--gauge-only", action="store_true", help="run gauge-force and link-update kernels and exit")
     ap.add_argument("--prec", default="f16")
     ap.add_argument("--clover", action="store_true", help="with --dslash-only: the clover normal operator")
     ap.add_argument("--recon", type=int, default=12)
@@ -626,6 +712,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-multi-rhs", action="store_true", help="skip the multi-RHS and batched solves")
     ap.add_argument("--skip-clover", action="store_true", help="skip the clover-operator measurements")
+    ap.add_argument("--skip-hmc", action="store_true", help="skip the HMC trajectory measurement")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loop from the host instead of one conditional CUDA graph (ncu cannot "
                          "profile kernels inside graphs with conditional nodes)")
@@ -634,6 +721,8 @@ def main():
     args = ap.parse_args()
     if args.dslash_only:
         run_dslash_only(args)
+    elif args.gauge_only:
+        run_gauge_only(args)
     elif args.solve_only:
         run_solve_only(args)
     elif args.impl == "reference":

@@ -252,7 +252,8 @@ cola_status cola_gauge_force(cola_gauge g, double beta, double *force_dev, cudaS
 /* links_dev (canonical FP64 [4][V][3][3], device, the field the handle was
  * created or last updated from) <- exp(i eps P) U link by link, then the
  * handle is re-packed from it (and its clover term rebuilt) as by
- * cola_gauge_update.  The exponential is a scaled Taylor series in FP64. */
+ * cola_gauge_update.  The exponential is exact to FP64 rounding (power series
+ * reduced by Cayley-Hamilton to three scalars, with scaling and squaring). */
 cola_status cola_link_update(cola_gauge g, void *links_dev, const double *mom_dev, double eps,
                              cudaStream_t stream);
 
@@ -263,8 +264,10 @@ typedef struct {
     double tau;             /* trajectory length */
     int nsteps;             /* integration steps (step eps = tau / nsteps) */
     int integrator;         /* COLA_INT_LEAPFROG, or COLA_INT_OMELYAN (2MN, lambda = 0.1931833275037836) */
-    double uniform;         /* Metropolis random number in [0, 1): accept if uniform < exp(-dH) */
-    cola_solver_params md;  /* force solves of D^dag D (op and system are set to FULL and NORMAL) */
+    double uniform;         /* Metropolis random number in [0, 1): accept if uniform <= exp(-dH) (0: always) */
+    cola_solver_params md;  /* force solves X = (D^dag D)^-1 phi: op COLA_OP_FULL runs CG on D^dag D;
+                               op COLA_OP_EO solves D W = gamma5 phi, then D X = gamma5 W, each
+                               through the even-odd Schur complement (system is set per solve) */
     double action_tol;      /* tolerance of the final action solve */
 } cola_hmc_params;
 
@@ -288,7 +291,7 @@ typedef struct {
  * momentum step eps/2; Omelyan 2MN: p -= lam eps F; U <- exp(i eps/2 P) U;
  * p -= (1 - 2 lam) eps F; U <- exp(i eps/2 P) U; p -= lam eps F, the two
  * adjacent lam steps of consecutive steps merged), F = dS_G/deps +
- * dS_F/deps with X = (D^dag D)^-1 phi solved from a zero guess; then H1 and
+ * dS_F/deps with X = (D^dag D)^-1 phi solved from a zero guess (see md); then H1 and
  * the Metropolis test.  On rejection links_dev and the handle are restored
  * bitwise.  Waits for the stream. */
 cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, const void *eta_dev,

@@ -26,7 +26,8 @@ eps = tau / n:
   Omelyan 2MN (Omelyan, Mryglod and Folk 2003), per step:
              p -= lam eps F; U <- exp(i eps/2 P) U; p -= (1 - 2 lam) eps F;
              U <- exp(i eps/2 P) U; p -= lam eps F,  lam = 0.1931833275037836.
-Metropolis: accept when the uniform number u < exp(-dH).
+Metropolis: accept when the uniform number u <= exp(-dH) (probability
+min(1, exp(-dH)) for u uniform on [0, 1); u = 0 always accepts).
 """
 from __future__ import annotations
 
@@ -158,5 +159,33 @@ def trajectory(u, p, eta, beta, kappa, bc, tau, nsteps, integrator="leapfrog", u
     h0 = kinetic(p) + gauge_action(u, beta) + (0.0 if eta is None else float(np.sum(np.abs(eta) ** 2)))
     u1, p1 = integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator, tol)
     dh = hamiltonian(u1, p1, phi, beta, kappa, bc, tol) - h0
-    accept = bool(uniform < np.exp(-dh))
+    accept = bool(uniform <= np.exp(-dh))
     return (u1 if accept else np.array(u, copy=True)), dh, accept
+
+
+def gauge_force_links(u, beta, links):
+    """dS_G/deps^a for a list of (mu, lexicographic site) links, by explicit site arithmetic: [n, 8]."""
+    _, lt, lz, ly, lx = u.shape[:5]
+    dims = (lx, ly, lz, lt)
+
+    def at(c, mu, step):
+        p = [(c[k] + step[k]) % dims[k] for k in range(4)]
+        return u[mu, p[3], p[2], p[1], p[0]]
+
+    out = np.zeros((len(links), 8))
+    for n, (mu, i) in enumerate(links):
+        i = int(i)
+        c = [i % lx, (i // lx) % ly, (i // (lx * ly)) % lz, i // (lx * ly * lz)]
+        v = np.zeros((3, 3), dtype=np.complex128)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            e_mu = [int(k == mu) for k in range(4)]
+            e_nu = [int(k == nu) for k in range(4)]
+            m_nu = [-x for x in e_nu]
+            v += at(c, nu, e_mu) @ at(c, mu, e_nu).conj().T @ at(c, nu, [0, 0, 0, 0]).conj().T
+            v += (at(c, nu, [a + b for a, b in zip(e_mu, m_nu)]).conj().T @ at(c, mu, m_nu).conj().T
+                  @ at(c, nu, m_nu))
+        w = at(c, mu, [0, 0, 0, 0]) @ v
+        out[n] = beta / 3.0 * np.einsum("kab,ba->k", T_GEN, w).imag
+    return out

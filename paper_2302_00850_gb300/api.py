@@ -312,9 +312,12 @@ def link_update(g: Gauge, links: torch.Tensor, mom: torch.Tensor, eps: float) ->
 
 def hmc_trajectory(g: Gauge, links: torch.Tensor, mom: torch.Tensor, eta: torch.Tensor | None, beta: float,
                    tau: float, nsteps: int, integrator="leapfrog", uniform=0.5, md_tol=1e-10, md_inner="f64",
-                   delta=0.1, action_tol=1e-12, use_graph=True) -> HmcInfo:
-    """One HMC update (see cola_hmc_trajectory); links and mom are updated in place."""
-    md = _lib.SolverParams(float(md_tol), 100000, OPS["full"], SYSTEMS["normal"], PREC[md_inner], float(delta), 1,
+                   delta=0.1, action_tol=1e-12, use_graph=True, md_op="full") -> HmcInfo:
+    """One HMC update (see cola_hmc_trajectory); links and mom are updated in place.
+
+    md_op "full": force solves by CG on D^dag D; "eo": two even-odd Dirac-system solves.
+    """
+    md = _lib.SolverParams(float(md_tol), 100000, OPS[md_op], SYSTEMS["normal"], PREC[md_inner], float(delta), 1,
                            int(bool(use_graph)))
     prm = _lib.HmcParams(float(beta), float(tau), int(nsteps), INTEGRATORS[integrator], float(uniform), md,
                          float(action_tol))

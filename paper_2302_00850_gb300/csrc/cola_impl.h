@@ -152,6 +152,8 @@ cudaError_t launch_plaquette_sum(const Geom &g, const void *links_f64, int recon
 // *out = scale * sum_k a[k] b[k] (device), deterministic
 cudaError_t launch_dot(const double *a, const double *b, size_t n, double scale, double *scratch, double *out,
                        cudaStream_t s);
+// out = gamma5 in on one canonical FP64 spinor field
+cudaError_t launch_gamma5(const Geom &g, void *out, const void *in, cudaStream_t s);
 // canonical links U_mu(x) <- exp(i eps P_mu(x)) U_mu(x)
 cudaError_t launch_link_update(const Geom &g, void *links_canon, const double *mom, double eps, cudaStream_t s);
 

@@ -143,34 +143,63 @@ __global__ void __launch_bounds__(kRedThreads) finish_sum_kernel(const double *p
     if (threadIdx.x == 0) out[0] = scale * t;
 }
 
-// E = exp(A) for anti-Hermitian A: scaling by 2^-s until the Frobenius norm
-// is at most 1/2, a degree-14 Taylor polynomial (remainder below 1e-17 at
-// that norm) by Horner's rule, then s squarings.
-__device__ void exp_antihermitian(Cx<double> (&a)[9], Cx<double> (&e)[9]) {
+// E = exp(A) for traceless 3x3 A (here anti-Hermitian).  By Cayley-Hamilton,
+// A^3 = s A + d I with s = tr(A^2) / 2 and d = det A, so every power is
+// A^k = al_k I + be_k A + ga_k A^2 with
+//   (al, be, ga)_{k+1} = (ga_k d, al_k + ga_k s, be_k),
+// and exp(A) = a I + b A + c A^2 with (a, b, c) = sum_k (al, be, ga)_k / k!:
+// a scalar series (three complex numbers) and one 3x3 product.  A is first
+// scaled by 2^-q to a Frobenius norm of at most 1 (30 terms then leave a
+// remainder below 1e-32 of the sum) and the result squared q times.
+__device__ void exp_traceless(Cx<double> (&a)[9], Cx<double> (&e)[9]) {
     double n2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) n2 += a[k].re * a[k].re + a[k].im * a[k].im;
-    int s = 0;
-    double nrm = sqrt(n2);
-    while (nrm > 0.5 && s < 60) {
-        nrm *= 0.5;
-        ++s;
+    int q = 0;
+    while (n2 > 1.0 && q < 60) {
+        n2 *= 0.25;
+        ++q;
     }
-    const double sc = ldexp(1.0, -s);
+    const double sc = ldexp(1.0, -q);
 #pragma unroll
     for (int k = 0; k < 9; ++k) a[k] = {a[k].re * sc, a[k].im * sc};
-    // Horner: e = I + a/1 (I + a/2 (I + ... (I + a/14)))
-#pragma unroll
-    for (int k = 0; k < 9; ++k) e[k] = {(k % 4 == 0) ? 1.0 : 0.0, 0.0};
-    for (int j = 14; j >= 1; --j) {
-        Cx<double> t[9];
-        mat3_set(t, a, false);
-        mat3_rmul(t, e, false);  // t = a e
-        const double r = 1.0 / j;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) e[k] = {((k % 4 == 0) ? 1.0 : 0.0) + t[k].re * r, t[k].im * r};
+    Cx<double> a2[9];
+    mat3_set(a2, a, false);
+    mat3_rmul(a2, a, false);
+    const Cx<double> s = {0.5 * (a2[0].re + a2[4].re + a2[8].re), 0.5 * (a2[0].im + a2[4].im + a2[8].im)};
+    // det A by cofactors of the first row
+    Cx<double> d = cmul(a[0], Cx<double>{cmul(a[4], a[8]).re - cmul(a[5], a[7]).re,
+                                         cmul(a[4], a[8]).im - cmul(a[5], a[7]).im});
+    {
+        const Cx<double> m1 = {cmul(a[3], a[8]).re - cmul(a[5], a[6]).re, cmul(a[3], a[8]).im - cmul(a[5], a[6]).im};
+        const Cx<double> m2 = {cmul(a[3], a[7]).re - cmul(a[4], a[6]).re, cmul(a[3], a[7]).im - cmul(a[4], a[6]).im};
+        const Cx<double> t1 = cmul(a[1], m1), t2 = cmul(a[2], m2);
+        d = {d.re - t1.re + t2.re, d.im - t1.im + t2.im};
     }
-    for (int q = 0; q < s; ++q) {
+    // k = 0: (1, 0, 0); the running term (al, be, ga) / k!
+    Cx<double> al = {1.0, 0.0}, be = {0.0, 0.0}, ga = {0.0, 0.0};
+    Cx<double> ca = al, cb = be, cc = ga;
+    for (int k = 1; k <= 30; ++k) {
+        const double r = 1.0 / k;
+        const Cx<double> gd = cmul(ga, d), gs = cmul(ga, s);
+        const Cx<double> nal = {gd.re * r, gd.im * r};
+        const Cx<double> nbe = {(al.re + gs.re) * r, (al.im + gs.im) * r};
+        const Cx<double> nga = {be.re * r, be.im * r};
+        al = nal;
+        be = nbe;
+        ga = nga;
+        ca = {ca.re + al.re, ca.im + al.im};
+        cb = {cb.re + be.re, cb.im + be.im};
+        cc = {cc.re + ga.re, cc.im + ga.im};
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Cx<double> v = cmul(cb, a[k]);
+        cmac(v, cc, a2[k]);
+        if (k % 4 == 0) v = {v.re + ca.re, v.im + ca.im};
+        e[k] = v;
+    }
+    for (int j = 0; j < q; ++j) {
         Cx<double> t[9];
         mat3_set(t, e, false);
         mat3_rmul(t, e, false);
@@ -196,13 +225,25 @@ __global__ void __launch_bounds__(kThreads) link_update_kernel(int V, double2 *l
     Cx<double> a[9], e[9], u[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) a[k] = {-eps * P[k].im, eps * P[k].re};
-    exp_antihermitian(a, e);
+    exp_traceless(a, e);
     double2 *lu = links + l * 9;
 #pragma unroll
     for (int k = 0; k < 9; ++k) u[k] = {lu[k].x, lu[k].y};
     mat3_rmul(e, u, false);
 #pragma unroll
     for (int k = 0; k < 9; ++k) lu[k] = make_double2(e[k].re, e[k].im);
+}
+
+// out = gamma5 in on canonical spinors (gamma5 = diag(1, 1, -1, -1) in the
+// chiral basis): spins 2 and 3 change sign
+__global__ void __launch_bounds__(kThreads) gamma5_kernel(int V, double2 *out, const double2 *in) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const double2 v = in[(size_t)i * 12 + c];
+        out[(size_t)i * 12 + c] = c < 6 ? v : make_double2(-v.x, -v.y);
+    }
 }
 
 int red_blocks(size_t n) {
@@ -241,6 +282,12 @@ cudaError_t launch_dot(const double *a, const double *b, size_t n, double scale,
     const int nb = red_blocks(n);
     dot_kernel<<<nb, kRedThreads, 0, s>>>(a, b, n, scratch);
     finish_sum_kernel<<<1, kRedThreads, 0, s>>>(scratch, nb, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma5(const Geom &g, void *out, const void *in, cudaStream_t s) {
+    gamma5_kernel<<<(g.V + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.V, static_cast<double2 *>(out),
+                                                                       static_cast<const double2 *>(in));
     return cudaGetLastError();
 }
 

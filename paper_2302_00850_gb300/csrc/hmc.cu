@@ -87,16 +87,34 @@ struct Traj {
     int cg_iters = 0;
 };
 
-// X = (D^dag D)^-1 phi from a zero guess, to tolerance tol
+// X = (D^dag D)^-1 phi from a zero guess, to tolerance tol.  md.op FULL: CG
+// on D^dag D.  md.op EO: X = D^-1 gamma5 D^-1 gamma5 phi (D^-dag =
+// gamma5 D^-1 gamma5), two Dirac-system solves through the even-odd Schur
+// complement, each on half the lattice with a better conditioned operator;
+// Y is scratch until the caller sets Y = D X.
 cola_status solve_x(Traj &T, double tol) {
+    const Geom &G = T.g->geom;
     cola_solver_params md = T.prm->md;
-    md.op = COLA_OP_FULL;
-    md.system = COLA_SYS_NORMAL;
     md.nrhs = 1;
     md.tol = tol;
-    HMC_CUDA(cudaMemsetAsync(T.X, 0, spinor_canon_bytes(T.g->geom), T.s), "zero guess");
     cola_solve_info info;
-    cola_status st = cola_cg_solve(T.g, T.X, T.phi, &md, &info, T.s);
+    if (md.op != COLA_OP_EO) {
+        md.op = COLA_OP_FULL;
+        md.system = COLA_SYS_NORMAL;
+        HMC_CUDA(cudaMemsetAsync(T.X, 0, spinor_canon_bytes(G), T.s), "zero guess");
+        cola_status st = cola_cg_solve(T.g, T.X, T.phi, &md, &info, T.s);
+        T.cg_iters += info.iters;
+        return st;
+    }
+    md.system = COLA_SYS_DIRAC;
+    HMC_CUDA(launch_gamma5(G, T.Y, T.phi, T.s), "gamma5");
+    HMC_CUDA(cudaMemsetAsync(T.X, 0, spinor_canon_bytes(G), T.s), "zero guess");
+    cola_status st = cola_cg_solve(T.g, T.X, T.Y, &md, &info, T.s);
+    T.cg_iters += info.iters;
+    if (st != COLA_OK) return st;
+    HMC_CUDA(launch_gamma5(G, T.Y, T.X, T.s), "gamma5");
+    HMC_CUDA(cudaMemsetAsync(T.X, 0, spinor_canon_bytes(G), T.s), "zero guess");
+    st = cola_cg_solve(T.g, T.X, T.Y, &md, &info, T.s);
     T.cg_iters += info.iters;
     return st;
 }
@@ -242,6 +260,8 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
     HMC_TRY(ws_slot(g, k + 0, link_canon_bytes(G), &T.saved));
     HMC_TRY(red_scratch(g, &T.scratch, &T.res));
     if (eta_dev) {
+        if (params->md.op != COLA_OP_FULL && params->md.op != COLA_OP_EO)
+            return arg_error("md.op must be COLA_OP_FULL or COLA_OP_EO");
         HMC_TRY(ws_slot(g, k + 1, sp, &T.phi));
         HMC_TRY(ws_slot(g, k + 2, sp, &T.X));
         HMC_TRY(ws_slot(g, k + 3, sp, &T.Y));
@@ -255,7 +275,7 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
     HMC_TRY(integrate(T));
     HMC_TRY(hamiltonian(T, true, &h1, &plaq));
     const double dh = h1 - h0;
-    const bool accept = params->uniform < std::exp(-dh);
+    const bool accept = params->uniform <= std::exp(-dh);  // NaN rejects
     if (!accept) {
         HMC_CUDA(cudaMemcpyAsync(links_dev, T.saved, link_canon_bytes(G), cudaMemcpyDeviceToDevice, stream),
                  "restore links");

@@ -69,9 +69,10 @@ def test_link_update(cola, eps):
     assert rel_err(got, oracle.dirac(want, psi, KAPPA, BC_AP)) < 1e-13
 
 
-@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
-@pytest.mark.parametrize("fermions", [False, True])
-def test_trajectory_matches_oracle(cola, integrator, fermions):
+@pytest.mark.parametrize("integrator,fermions,md_op", [("leapfrog", False, "full"), ("omelyan", False, "full"),
+                                                        ("leapfrog", True, "full"), ("omelyan", True, "full"),
+                                                        ("omelyan", True, "eo")])
+def test_trajectory_matches_oracle(cola, integrator, fermions, md_op):
     dims = (4, 4, 4, 4)
     u = synth.gauge_field(dims, 0.3, synth.seed_for(98, 4))
     p = momenta(dims, 5)
@@ -83,7 +84,7 @@ def test_trajectory_matches_oracle(cola, integrator, fermions):
     ud, pd = to_dev(u), to_dev(p)
     g = gauge(cola, ud, dims)
     info = cola.hmc_trajectory(g, ud, pd, None if eta is None else to_dev(eta), BETA, tau, n, integrator,
-                               uniform=0.0, md_tol=1e-13, action_tol=1e-13)
+                               uniform=0.0, md_tol=1e-13, action_tol=1e-13, md_op=md_op)
     assert info.accepted
     assert info.force_evals == (n + 1 if integrator == "leapfrog" else 2 * n + 1)
     assert np.max(np.abs(ud.cpu().numpy() - u1)) < 1e-10

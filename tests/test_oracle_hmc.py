@@ -116,4 +116,14 @@ def test_trajectory_start_and_metropolis():
     assert acc and not np.array_equal(u_acc, u)
     u_rej, dh2, acc2 = hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.3, 3, uniform=1.0 - 1e-300)
     assert dh2 == dh
-    assert acc2 == (dh < 0) and (acc2 or np.array_equal(u_rej, u))
+    assert acc2 == (dh <= 0) and (acc2 or np.array_equal(u_rej, u))
+
+
+def test_gauge_force_links_matches_whole_lattice():
+    dims = (4, 6, 2, 4)
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(97, 15))
+    full = hmc.gauge_force(u, 5.7).reshape(4, -1, 8)
+    links = [(mu, i) for mu in range(4) for i in range(0, full.shape[1], 7)]
+    got = hmc.gauge_force_links(u, 5.7, links)
+    want = np.array([full[mu, i] for mu, i in links])
+    assert np.max(np.abs(got - want)) < 1e-13
