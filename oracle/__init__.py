@@ -16,7 +16,8 @@ definitions, each stated where it is coded:
   wilson.py  gamma matrices, hopping term H, D = 1 - kappa H, H^dagger,
              even-odd blocks and the Schur operator Mhat, sampled-site H
   solve.py   Hestenes-Stiefel CG with true-residual confirmation, the
-             even-odd normal-equation solve, dense matrices for brute force
+             even-odd normal-equation solve, shifted systems (A + sigma_i) x_i = b
+             one CG per shift, dense matrices for brute force
   force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
   clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H
              and its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe
@@ -42,5 +43,5 @@ from .wilson import (  # noqa: F401
     dirac, dirac_dag, hop_block, mhat, mhat_dag, mdagm_full, mdagm_eo,
     hop_sites, gamma5_apply,
 )
-from .solve import cg, solve_normal_full, solve_normal_eo, solve_dirac_eo, dense_matrix  # noqa: F401
+from .solve import cg, solve_normal_full, solve_normal_eo, solve_dirac_eo, solve_shifted, dense_matrix  # noqa: F401
 from .force import GELL_MANN, T_GEN, force_coeffs, dirac_link_grad, link_variation  # noqa: F401

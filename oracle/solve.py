@@ -100,3 +100,14 @@ def dense_matrix(apply_op, shape):
         m[:, j] = apply_op(e.reshape(shape)).reshape(-1)
         e[j] = 0.0
     return m
+
+
+def solve_shifted(apply_a, b, shifts, tol=1e-10, max_iter=100000):
+    """x_i = (A + sigma_i)^-1 b for every shift, each by its own CG (the definition
+    a multi-shift solver must reproduce).  Returns ([x_i], [true relative residual])."""
+    xs, res = [], []
+    for sigma in shifts:
+        x, _, r = cg(lambda v, s=sigma: apply_a(v) + s * v, b, None, tol, max_iter)
+        xs.append(x)
+        res.append(r)
+    return xs, res

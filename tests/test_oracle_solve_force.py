@@ -135,3 +135,24 @@ def test_link_gradient_against_finite_differences():
             d = (loss(up) - loss(um)) / (2 * h)
             want = g[idx].real if part == "re" else g[idx].imag
             assert abs(d - want) < 1e-8 * max(1.0, abs(want))
+
+
+def test_shifted_solves_against_dense(small):
+    dims, u, b = small
+    kappa = 0.124
+    e = oracle.even_mask(dims)[..., None, None]
+    be = b * e
+    shifts = [0.0, 0.01, 0.3, 2.5]
+    op = lambda v: oracle.mdagm_eo(u, v * e, kappa, BC_AP) * e  # noqa: E731
+    xs, res = oracle.solve_shifted(op, be, shifts, tol=1e-12)
+    par = np.repeat(oracle.parity_of_sites(dims).reshape(-1), 12)
+    ev = np.where(par == 0)[0]
+    a = oracle.dense_matrix(op, b.shape)[np.ix_(ev, ev)]
+    for sigma, x, r in zip(shifts, xs, res):
+        m = a + sigma * np.eye(len(ev))
+        want = np.linalg.solve(m, be.reshape(-1)[ev])
+        assert r <= 1e-12
+        assert norm(x.reshape(-1)[ev] - want) / norm(want) < np.linalg.cond(m) * 1e-12
+    # larger shifts give smaller solutions (A + sigma is positive definite, growing with sigma)
+    norms = [norm(x) for x in xs]
+    assert all(n1 > n2 for n1, n2 in zip(norms, norms[1:]))
