@@ -213,6 +213,21 @@ cola_status cola_cg_solve_batched(int nlat, const cola_gauge *gauges, void *cons
                                   const void *const *b_dev, const cola_solver_params *params,
                                   cola_solve_info *info, cudaStream_t stream);
 
+/* Multi-shift CG: x_i = (A + shifts[i])^-1 b for nshift (1..64) shifts >= 0
+ * at once, A = Mhat^dag Mhat (op COLA_OP_EO, even sites; odd sites of x set
+ * to zero) or D^dag D (COLA_OP_FULL); the partial-fraction building block
+ * of rational HMC.  x_dev: canonical FP64 [nshift][V][4][3] (device, output;
+ * no initial guess); b_dev: canonical [V][4][3]; shifts: host array.
+ * Phase 1 runs the shifted-CG recurrence (Jegerlehner 1996) on one Krylov
+ * space in params->inner storage down to tol_sloppy (0: tol for FP64, else
+ * max(tol, 1e-6)); phase 2 refines all shifts together with the
+ * mixed-precision CG of cola_cg_solve (rows = shifts, FP64 reliable updates,
+ * FP64 true residual) down to params->tol.  params: system must be NORMAL;
+ * nrhs ignored.  info: nshift entries (host); iters counts both phases. */
+cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const void *b_dev, const double *shifts,
+                                  int nshift, double tol_sloppy, const cola_solver_params *params,
+                                  cola_solve_info *info, cudaStream_t stream);
+
 /* Fermion force of S = phi^dag (D^dag D)^-1 phi given X = (D^dag D)^-1 phi and
  * Y = D X (canonical FP64, device).  Output force_dev: real FP64 [4][V][8],
  * F^a_mu(x) = dS/d eps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x), T^a = lambda^a/2:

@@ -84,6 +84,8 @@ SIGNATURES = {
     "cola_cg_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_cg_solve_batched": (_st, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                      ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
+    "cola_multishift_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _i, _d,
+                                     ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_fermion_force": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_dirac_link_grad": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_plaquette": (_st, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),

@@ -248,6 +248,27 @@ def cg_solve_batched(gauges, bs, x0s=None, tol=1e-10, max_iter=100000, op="eo", 
     return xs, res
 
 
+def multishift_solve(g: Gauge, b: torch.Tensor, shifts, tol=1e-10, max_iter=100000, op="eo", inner="f64",
+                     delta=0.1, tol_sloppy=0.0, use_graph=False, raise_on_error=True):
+    """x_i = (A + shifts[i])^-1 b for all shifts at once (see cola_multishift_solve).
+
+    Returns (x [nshift, Lt, Lz, Ly, Lx, 4, 3] complex128, [SolveInfo per shift]).
+    """
+    shifts = [float(v) for v in shifts]
+    n = len(shifts)
+    x = torch.empty((n,) + g.spinor_shape(), dtype=torch.complex128, device=g.device)
+    prm = _lib.SolverParams(float(tol), int(max_iter), OPS[op], SYSTEMS["normal"], PREC[inner], float(delta), 1,
+                            int(bool(use_graph)))
+    infos = (_lib.SolveInfo * n)()
+    sh = (ctypes.c_double * n)(*shifts)
+    st = g.lib.cola_multishift_solve(g.handle, _ptr(x), _complex_field(b, g.volume * 12, "b"), sh, n,
+                                     float(tol_sloppy), ctypes.byref(prm), infos, _stream(g.device))
+    res = [SolveInfo(i.iters, i.reliable_updates, i.true_rel_resid, i.seconds, i.status) for i in infos]
+    if st != 0 and (raise_on_error or st not in (-4, -5)):
+        check(st)
+    return x, res
+
+
 def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
     """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X."""
     lx, ly, lz, lt = g.dims

@@ -90,6 +90,14 @@ __global__ void __launch_bounds__(kBlasBlock) cg_update_xr_kernel(const __grid_c
         SpinorIO<PX>::load(vptr(B, r, 0), vh, r.cb, xv);
         const RV a = (RV)alpha;
         const RX ax = (RX)alpha;
+        if (S.shift != 0.0) {  // q + sigma p is the shifted operator's A p
+            const RV sg = (RV)S.shift;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                qv[k].re = fma(sg, pv[k].re, qv[k].re);
+                qv[k].im = fma(sg, pv[k].im, qv[k].im);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             xv[k].re += ax * (RX)pv[k].re;
@@ -124,15 +132,20 @@ __global__ void __launch_bounds__(kBlasBlock) cg_update_p_kernel(const __grid_co
     SpinorIO<PV>::store(vptr_w(B, r, 0), vh, r.cb, pv);
 }
 
-// slot (mp):  partial |M p|^2 = <p, A p>
+// slots (mp, p):  partial |M p|^2 = <p, A p>  (+ sigma |p|^2 for a shifted row)
 template <int PV>
 __global__ void __launch_bounds__(kBlasBlock) cg_pq_kernel(const __grid_constant__ BlasArgs B) {
     const SiteRef r = blas_site(B);
+    const CgState &S = B.state[r.row];
     double nr = 0.0;
-    if (!B.state[r.row].done && r.ok) {
+    if (!S.done && r.ok) {
         Cx<typename Prec<PV>::real> m[12];
         SpinorIO<PV>::load(vptr(B, r, 0), B.lat[r.l].vh, r.cb, m);
         nr = site_norm2(m);
+        if (S.shift != 0.0) {
+            SpinorIO<PV>::load(vptr(B, r, 1), B.lat[r.l].vh, r.cb, m);
+            nr += S.shift * site_norm2(m);
+        }
     }
     write_partial(B, r, nr);
 }
@@ -163,16 +176,27 @@ __device__ __forceinline__ bool ru_live(const BlasArgs &B, const CgState &S) {
     return B.init ? true : (S.ru && !S.done);
 }
 
-// slots (r_hi, b, ax, r_lo, p):  r_hi = b - ax;  r_lo = r_hi;  (init: p = r_lo);  partial |r_hi|^2
+// slots (r_hi, b, ax, r_lo, p, x_hi):  r_hi = b - ax (- sigma x_hi);  r_lo = r_hi;  (init: p = r_lo);
+// partial |r_hi|^2
 template <int PV>
 __global__ void __launch_bounds__(kBlasBlock) ru_residual_kernel(const __grid_constant__ BlasArgs B) {
     const SiteRef r = blas_site(B);
+    const CgState &S = B.state[r.row];
     double nr = 0.0;
-    if (ru_live(B, B.state[r.row]) && r.ok) {
+    if (ru_live(B, S) && r.ok) {
         const int vh = B.lat[r.l].vh;
         Cx<double> bv[12], av[12];
         SpinorIO<COLA_F64>::load(vptr(B, r, 1), vh, r.cb, bv);
         SpinorIO<COLA_F64>::load(vptr(B, r, 2), vh, r.cb, av);
+        if (S.shift != 0.0) {
+            Cx<double> xv[12];
+            SpinorIO<COLA_F64>::load(vptr(B, r, 5), vh, r.cb, xv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                av[k].re = fma(S.shift, xv[k].re, av[k].re);
+                av[k].im = fma(S.shift, xv[k].im, av[k].im);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             bv[k].re -= av[k].re;

@@ -94,7 +94,7 @@ cudaError_t launch_unpack_spinor(int prec, const Geom &g, void *canon, const voi
 // meaning depends on the kernel), all of the precision prec[slot].  Each
 // lattice covers nparity parity blocks (1: even half only; 2: whole lattice)
 // of nrhs right-hand sides; rows are row0 + rhs.
-constexpr int kMaxVecs = 5;
+constexpr int kMaxVecs = 6;
 
 struct BlasLat {
     int vh;
@@ -118,8 +118,12 @@ struct BlasArgs {
     int init;             // ru_residual: initial residual (every row, also writes p)
 };
 
-// Slots: update_xr (x, r, p, q); update_p (p, r); pq (mp); ru_accumulate (x_hi, x_lo);
-// ru_residual (r_hi, b, ax, r_lo, p); norm2 (v); convert (dst, src); axpby (dst, x, y).
+// Slots: update_xr (x, r, p, q); update_p (p, r); pq (mp, p); ru_accumulate (x_hi, x_lo);
+// ru_residual (r_hi, b, ax, r_lo, p, x_hi); norm2 (v); convert (dst, src); axpby (dst, x, y).
+// A row with CgState::shift = sigma != 0 solves (A + sigma) x = b: pq adds
+// sigma |p|^2 (reading p), update_xr subtracts alpha (q + sigma p), and
+// ru_residual subtracts sigma x_hi (reading x_hi); rows with sigma = 0 read
+// and compute exactly what the unshifted solver does.
 cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s);         // slot (mp): pq, rho, alpha
@@ -181,6 +185,7 @@ struct cola_gauge_s {
     static constexpr int kSlotCloverFlag = kSlots - 1;  // the construction's pivot flag
     // HMC: saved links, phi, X, Y, two packed FP64 fields, reduction scratch
     static constexpr int kSlotHmc = 15;
+    static constexpr int kSlotMultishift = 22;  // the multi-shift solver's workspace block
     void *slot[kSlots] = {};
     size_t slot_bytes[kSlots] = {};
     double *partials = nullptr;
@@ -221,6 +226,11 @@ void set_clover(DslashLat &L, cola_gauge g, int prec, bool inverse);
 // Launch a (batched) hopping term with the links of `owner`'s reconstruction.
 cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity, bool dagger, int epi,
                           cudaStream_t s);
+// The CG solve of one lattice with per-right-hand-side shifts: row r solves
+// (A + shifts[r]) x_r = b_r (shifts may be null); shared_b: b holds one field
+// used by every row.  x holds the initial guesses on entry.
+cola_status cg_solve_rows(cola_gauge g, void *x, const void *b, const cola_solver_params *prm, cola_solve_info *info,
+                          cudaStream_t s, const double *shifts, bool shared_b);
 // (Re)builds g's clover fields from its FP64 links (g->csw != 0); waits for
 // the construction to read its pivot flag.
 cola_status clover_rebuild(cola_gauge g, cudaStream_t s);

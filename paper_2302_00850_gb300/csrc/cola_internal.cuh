@@ -551,6 +551,7 @@ struct CgState {
     double b2;       // |b|^2
     double tol2;     // tol^2 |b|^2
     double delta2;   // delta^2
+    double shift;    // sigma: this row solves (A + sigma) x = b
     int iter;
     int max_iter;
     int ru;          // a reliable update is due

@@ -129,14 +129,15 @@ cola_status ru_block(const SolveCtx &c, cudaStream_t s) {
     BlasArgs B = blas(c, {{V_XHI, COLA_F64}, {V_XLO, c.xprec}});
     COLA_CUDA(launch_ru_accumulate(B, false, s), "reliable update (accumulate)");
     COLA_TRY(mdagm(c, COLA_F64, V_AX, V_XHI, V_T64, V_MP64, c.owner->states, true, s));
-    B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
+    B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec},
+                 {V_XHI, COLA_F64}});
     COLA_CUDA(launch_ru_residual(B, s), "reliable update (residual)");
     return COLA_OK;
 }
 
 cola_status iter_head(const SolveCtx &c, cudaStream_t s) {
     COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, s));
-    BlasArgs P = blas(c, {{V_MP, c.prec}});  // <p, A p> = |M p|^2, alpha
+    BlasArgs P = blas(c, {{V_MP, c.prec}, {V_P, c.prec}});  // <p, A p> = |M p|^2 (+ sigma |p|^2), alpha
     COLA_CUDA(launch_cg_pq(P, s), "cg <p, Ap>");
     BlasArgs B = blas(c, {{V_XLO, c.xprec}, {V_RLO, c.prec}, {V_P, c.prec}, {V_Q, c.prec}});
     COLA_CUDA(launch_cg_update_xr(B, s), "cg update x, r");
@@ -330,10 +331,15 @@ cola_status check_params(const cola_solver_params *prm) {
 
 // Solve every lattice of the batch together: one launch per kernel per
 // iteration covers all lattices and right-hand sides.
+// shifts (host, nrhs entries, may be null): right-hand side r solves
+// (A + shifts[r]) x = b (normal system only).  shared_b: bs[l] holds one field
+// that every right-hand side of lattice l solves with.
 cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const void *const *bs,
-                        const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s) {
+                        const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s,
+                        const double *shifts = nullptr, bool shared_b = false) {
     const auto t0 = std::chrono::steady_clock::now();
     COLA_TRY(check_params(prm));
+    if (shifts && prm->system != COLA_SYS_NORMAL) return arg_error("shifted solves need the normal system");
     SolveCtx c;
     std::memset(&c, 0, sizeof(c));
     c.nlat = nlat;
@@ -400,7 +406,11 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         const double k = g->lat.kappa;
         if (!dirac) {
             const int pmask = prm->op == COLA_OP_EO ? 1 : 3;
-            COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.b, bs[l], c.nrhs, pmask, s), "pack b");
+            COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.b, bs[l], shared_b ? 1 : c.nrhs, pmask, s), "pack b");
+            const size_t hi1 = 2 * spinor_parity_bytes(COLA_F64, G.Vh);
+            for (int r = 1; shared_b && r < c.nrhs; ++r)
+                COLA_CUDA(cudaMemcpyAsync(static_cast<char *>(L.b) + r * hi1, L.b, hi1, cudaMemcpyDeviceToDevice, s),
+                          "replicate b");
         } else {
             COLA_CUDA(launch_pack_spinor(COLA_F64, G, L.borig, bs[l], c.nrhs, 3, s), "pack b");
             if (prm->op == COLA_OP_EO) {
@@ -435,6 +445,7 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         st.tol2 = prm->tol * prm->tol;
         st.delta2 = prm->inner == COLA_F64 ? 0.0 : prm->delta * prm->delta;
         st.max_iter = prm->max_iter;
+        st.shift = shifts ? shifts[r % c.nrhs] : 0.0;
         st.status = COLA_ERR_NOT_CONVERGED;
     }
     COLA_CUDA(cudaMemcpyAsync(c.owner->states, hs, nrows * sizeof(CgState), cudaMemcpyHostToDevice, s),
@@ -467,7 +478,8 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         }
     }
     {
-        BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec}});
+        BlasArgs B = blas(c, {{V_RHI, COLA_F64}, {V_B, COLA_F64}, {V_AX, COLA_F64}, {V_RLO, c.prec}, {V_P, c.prec},
+                              {V_XHI, COLA_F64}});
         B.init = 1;
         COLA_CUDA(launch_ru_residual(B, s), "initial residual");
     }
@@ -561,6 +573,11 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
 }
 
 }  // namespace
+
+cola_status cg_solve_rows(cola_gauge g, void *x, const void *b, const cola_solver_params *prm, cola_solve_info *info,
+                          cudaStream_t s, const double *shifts, bool shared_b) {
+    return solve_batch(1, &g, &x, &b, prm, info, s, shifts, shared_b);
+}
 
 }  // namespace cola
 

@@ -126,6 +126,22 @@ def test_hmc_parameter_errors_before_any_cuda_call(lib):
     assert lib.cola_hmc_trajectory(None, fake, fake, None, None, ctypes.byref(info), None) == -1
 
 
+def test_multishift_parameter_errors_before_any_cuda_call(lib):
+    from paper_2302_00850_gb300 import _lib
+
+    fake = ctypes.c_void_p(1)
+    info = (_lib.SolveInfo * 2)()
+    good = (ctypes.c_double * 2)(0.0, 0.5)
+    bad = (ctypes.c_double * 2)(0.0, -0.5)
+    prm = _lib.SolverParams(1e-10, 100, 1, 0, 0, 0.1, 1, 0)
+    assert lib.cola_multishift_solve(None, fake, fake, good, 2, 0.0, ctypes.byref(prm), info, None) == -1
+    assert lib.cola_multishift_solve(fake, fake, fake, good, 0, 0.0, ctypes.byref(prm), info, None) == -1
+    assert lib.cola_multishift_solve(fake, fake, fake, good, 65, 0.0, ctypes.byref(prm), info, None) == -1
+    assert lib.cola_multishift_solve(fake, fake, fake, bad, 2, 0.0, ctypes.byref(prm), info, None) == -1
+    dirac = _lib.SolverParams(1e-10, 100, 1, 1, 0, 0.1, 1, 0)
+    assert lib.cola_multishift_solve(fake, fake, fake, good, 2, 0.0, ctypes.byref(dirac), info, None) == -1
+
+
 def test_solver_parameter_errors_before_any_cuda_call(lib):
     from paper_2302_00850_gb300 import _lib
 
