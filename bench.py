@@ -314,6 +314,7 @@ def run_cola(args):
     multi = None if args.skip_multi_rhs else multi_rhs_measurements(cola, dev)
     clover = None if args.skip_clover else clover_measurements(cola, dev, u, b)
     hmc = None if args.skip_hmc else hmc_measurements(cola, dev)
+    multishift = None if args.skip_multishift else multishift_measurements(cola, dev, u, b)
 
     # end to end through the public API with host buffers: every step copies
     # the canonical links and the source from pinned host memory, re-packs the
@@ -402,6 +403,7 @@ def run_cola(args):
             "multi_rhs": multi,
             "clover": clover,
             "hmc": hmc,
+            "multishift": multishift,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -614,6 +616,50 @@ def hmc_measurements(cola, dev):
     }
 
 
+def multishift_measurements(cola, dev, u, b):
+    """Multi-shift CG on the benchmark's lattice (not part of the timed step).
+
+    Ten shifts sigma_i = 1e-4 x 10^(0.6 i) (1e-4 .. 25, the spread of a
+    rational approximation's poles) on Mhat^dag Mhat of the 32^3x64 workload,
+    to 1e-10 per shift: FP32 phase 1 (to 1e-7) plus the FP16-inner refinement
+    with FP64 reliable updates at delta = 0.01, against the same ten systems
+    solved one at a time by the same mixed solver, and against the plain FP64
+    multi-shift recurrence.
+    """
+    import torch
+
+    shifts = [1e-4 * 10 ** (0.6 * i) for i in range(10)]
+    g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f64", "f32", "f16"), recon={"f64": 18, "f32": 12, "f16": 12})
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    # warm-up of every variant timed below: launch-shape tuning and solve-graph capture per shape
+    mixed = dict(tol=TOL, op="eo", inner="f16", delta=0.01, use_graph=True)
+    cola.multishift_solve(g, b, shifts, **mixed)
+    cola.multishift_solve(g, b, shifts, tol=TOL, op="eo", inner="f64")
+    cola.multishift_solve(g, b, shifts[:1], **mixed)
+    ms16, (x16, i16) = timed(lambda: cola.multishift_solve(g, b, shifts, **mixed))
+    ms64, (x64, i64) = timed(lambda: cola.multishift_solve(g, b, shifts, tol=TOL, op="eo", inner="f64"))
+    sep = 0.0
+    for sg in shifts:
+        t, _ = timed(lambda sg=sg: cola.multishift_solve(g, b, [sg], **mixed))
+        sep += t
+    return {
+        "lattice": "32x32x32x64", "nshift": len(shifts), "shifts": [shifts[0], shifts[-1]], "tol": TOL,
+        "delta": 0.01, "phase1": "fp32 to 1e-7", "refinement": "fp16 inner, fp64 reliable updates",
+        "mixed_f16_ms": ms16, "max_true_rel_resid": max(i.true_rel_resid for i in i16),
+        "iters_smallest_shift": i16[0].iters, "iters_largest_shift": i16[-1].iters,
+        "fp64_ms": ms64, "separate_mixed_solves_ms": sep, "multishift_over_separate": ms16 / sep,
+    }
+
+
 def run_dslash_only(args):
     """Chained parity Dslash applies only (the case profiled with ncu)."""
     import torch
@@ -713,6 +759,7 @@ def main():
     ap.add_argument("--skip-multi-rhs", action="store_true", help="skip the multi-RHS and batched solves")
     ap.add_argument("--skip-clover", action="store_true", help="skip the clover-operator measurements")
     ap.add_argument("--skip-hmc", action="store_true", help="skip the HMC trajectory measurement")
+    ap.add_argument("--skip-multishift", action="store_true", help="skip the multi-shift CG measurement")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the CG loop from the host instead of one conditional CUDA graph (ncu cannot "
                          "profile kernels inside graphs with conditional nodes)")

@@ -219,11 +219,13 @@ cola_status cola_cg_solve_batched(int nlat, const cola_gauge *gauges, void *cons
  * of rational HMC.  x_dev: canonical FP64 [nshift][V][4][3] (device, output;
  * no initial guess); b_dev: canonical [V][4][3]; shifts: host array.
  * Phase 1 runs the shifted-CG recurrence (Jegerlehner 1996) on one Krylov
- * space in params->inner storage down to tol_sloppy (0: tol for FP64, else
- * max(tol, 1e-6)); phase 2 refines all shifts together with the
- * mixed-precision CG of cola_cg_solve (rows = shifts, FP64 reliable updates,
- * FP64 true residual) down to params->tol.  params: system must be NORMAL;
- * nrhs ignored.  info: nshift entries (host); iters counts both phases. */
+ * space down to tol_sloppy (0: tol for FP64, else max(tol, 1e-7)), in FP64
+ * when params->inner is COLA_F64 and in FP32 storage otherwise (the handle
+ * then needs FP32 links too); phase 2 refines all shifts together with the
+ * mixed-precision CG of cola_cg_solve in params->inner (rows = shifts, FP64
+ * reliable updates, FP64 true residual) down to params->tol.  params: system
+ * must be NORMAL; nrhs ignored.  info: nshift entries (host); iters counts
+ * both phases. */
 cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const void *b_dev, const double *shifts,
                                   int nshift, double tol_sloppy, const cola_solver_params *params,
                                   cola_solve_info *info, cudaStream_t stream);

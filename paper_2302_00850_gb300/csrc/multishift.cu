@@ -18,12 +18,14 @@
 // with zeta_0 = zeta_{-1} = 1, a_{-1} = 1, b_{-1} = 0.  Shift i has converged
 // when |zeta^i| |r| <= tol |b|; the base shift converges last.
 //
-// Phase 1 runs this recurrence with r and every p^i in the storage precision
-// (FP64, FP32 or FP16 with per-site scale; x^i in FP32 unless FP64) down to
-// tol_sloppy, with one operator application per iteration for all shifts.
-// Phase 2 refines every shift at once from those x^i with the mixed-precision
-// CG of solver.cu (one right-hand-side row per shift, row shifts sigma_i,
-// FP64 reliable updates and an FP64 true residual) down to tol.  All scalars
+// Phase 1 runs this recurrence with r, every p^i and x^i in FP32 storage (FP64
+// for a plain FP64 solve) down to tol_sloppy, with one operator application
+// per iteration for all shifts; FP16 storage is not used there, since
+// rounding every p^i to FP16 each iteration stalls the shifted solutions near
+// 1e-3 (measured).  Phase 2 refines every shift at once from those x^i with
+// the mixed-precision CG of solver.cu in the requested inner precision (one
+// right-hand-side row per shift, row shifts sigma_i, FP64 reliable updates
+// and an FP64 true residual) down to tol.  All scalars
 // live on the device; the host reads the state every few iterations.
 #include <algorithm>
 #include <chrono>
@@ -330,11 +332,14 @@ extern "C" cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const vo
     for (int i = 0; i < nshift; ++i)
         if (!std::isfinite(shifts[i]) || shifts[i] < 0.0) return arg_error("shifts must be finite and >= 0");
     const double tol1 = tol_sloppy > 0.0 ? std::max(tol_sloppy, prm->tol)
-                                         : (prm->inner == COLA_F64 ? prm->tol : std::max(prm->tol, 1e-6));
+                                         : (prm->inner == COLA_F64 ? prm->tol : std::max(prm->tol, 1e-7));
     if (!(tol1 < 1.0)) return arg_error("tol_sloppy must be below 1");
-    const int prec = prm->inner;
-    if (!g->links[COLA_F64] || !g->links[prec]) {
-        set_error("cola_multishift_solve needs FP64 links and links of the inner precision");
+    // phase 1 in FP64 for a plain FP64 solve, else in FP32 storage: rounding
+    // every p^i to FP16 each iteration stalls the shifted solutions near 1e-3
+    const int prec = prm->inner == COLA_F64 ? COLA_F64 : COLA_F32;
+    if (!g->links[COLA_F64] || !g->links[prec] || !g->links[prm->inner]) {
+        set_error("cola_multishift_solve needs FP64 links, and FP32 links plus links of the inner precision for a "
+                  "mixed-precision solve");
         return COLA_ERR_UNSUPPORTED;
     }
     const Geom &G = g->geom;

@@ -94,7 +94,7 @@ def test_fp64_phase_one_needs_no_refinement(cola):
 def test_single_shift_equals_shifted_solve(cola):
     dims = (4, 4, 4, 8)
     u, b = lattice_inputs(dims, eps=0.3, config=83)
-    g = cola.Gauge(to_dev(u), dims, KAPPA, BC_AP, precisions=("f64", "f16"))
+    g = cola.Gauge(to_dev(u), dims, KAPPA, BC_AP, precisions=("f64", "f32", "f16"))
     x, infos = cola.multishift_solve(g, to_dev(b), [0.25], tol=1e-10, op="eo", inner="f16")
     check_against_oracle(u, b, dims, "eo", [0.25], x.cpu().numpy(), infos, 1e-10, 1e-7)
 

@@ -1,0 +1,53 @@
+"""Multi-shift CG at the benchmark's size, 32^3x64 (GPU; slow test).
+
+The benchmark's ten shifts 1e-4 x 10^(0.6 i) on Mhat^dag Mhat of the 32^3x64
+workload (kappa 0.1245, links exp(0.25 i H)), FP32 phase 1 plus FP16
+refinement to 1e-10, in the launch configuration bench.py times.  The smallest shift
+(the slowest to converge) has its true residual recomputed by the oracle's
+whole-lattice operator; every shift's library residual must meet the target.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import BC_AP, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cola():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_00850_gb300 as cola
+    from paper_2302_00850_gb300 import build
+
+    build.build()
+    return cola
+
+
+def test_multishift_32x32x32x64(cola):
+    import torch
+
+    dims = (32, 32, 32, 64)
+    kappa = 0.1245
+    shifts = [1e-4 * 10 ** (0.6 * i) for i in range(10)]
+    u_dev = synth.gauge_field(dims, 0.25, synth.seed_for(2, 0), device="cuda", as_numpy=False)
+    b = synth.gaussian_spinor(dims, synth.seed_for(2, 1))
+    g = cola.Gauge(u_dev, dims, kappa, BC_AP, precisions=("f64", "f32", "f16"), recon={"f64": 18, "f32": 12, "f16": 12})
+    x, infos = cola.multishift_solve(g, to_dev(b), shifts, tol=1e-10, op="eo", inner="f16", use_graph=True)
+    assert all(i.status == 0 and i.true_rel_resid <= 1e-10 for i in infos)
+    its = [i.iters for i in infos]
+    assert its == sorted(its, reverse=True) or its[0] >= its[-1]
+    x0 = x[0].cpu().numpy()
+    u = u_dev.cpu().numpy()
+    del u_dev, g, x
+    torch.cuda.empty_cache()
+    e = oracle.even_mask(dims)[..., None, None]
+    res = rel_err(oracle.mdagm_eo(u, x0 * e, kappa, BC_AP) * e + shifts[0] * x0 * e, b * e)
+    assert res <= 1.05e-10, res
+    assert abs(res - infos[0].true_rel_resid) < 1e-12
+    assert np.max(np.abs(x0 * (1 - e))) == 0.0
