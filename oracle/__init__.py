@@ -23,6 +23,8 @@ definitions, each stated where it is coded:
              and its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe
   hmc.py     Wilson gauge action and force, momenta, leapfrog and Omelyan
              integrators, the Hamiltonian and the Metropolis step
+  eig.py     the lowest eigenpairs of D^dag D and Mhat^dag Mhat (dense and
+             Lanczos), and closed forms of both free-field spectra
 
 Pins (tests/test_oracle_*.py, run without a GPU): gamma algebra; the free
 field closed form (plane waves and the full D^dag D spectrum); gamma5
@@ -35,8 +37,9 @@ abelian field in closed form, the weak-field lattice curl, gauge covariance,
 dense Schur identities and the tree-level cancellation of the Wilson lift of
 Landau zero modes (which fixes its sign); for HMC the gauge force against
 finite differences of the action, exact free motion, reversibility and the
-second-order scaling of dH.  Every function here is pinned by at least one
-of them.
+second-order scaling of dH; for the eigenmodes the closed-form free-field
+spectra of D^dag D and Mhat^dag Mhat (derived in eig.py).  Every function
+here is pinned by at least one of them.
 """
 from .wilson import (  # noqa: F401
     GAMMA, GAMMA5, IDENTITY4, parity_of_sites, even_mask, phased_links, hop,
