@@ -230,6 +230,39 @@ cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const void *b_dev, 
                                   int nshift, double tol_sloppy, const cola_solver_params *params,
                                   cola_solve_info *info, cudaStream_t stream);
 
+/* Lowest eigenmodes of A = Mhat^dag Mhat (op COLA_OP_EO, even sites) or
+ * D^dag D (COLA_OP_FULL) by the accelerated conjugate-gradient method of
+ * Kalkreuter and Simma (1996), which the paper cites for COLA's eigensolver:
+ * each vector minimises the Ritz functional <x, A x> / <x, x> by CG in the
+ * complement of the ones before it, and every sweep ends with a
+ * Rayleigh-Ritz diagonalisation of A on the span of all nev vectors.  FP64.
+ * evecs_dev: canonical FP64 [nev][V][4][3] (device); on entry the caller's
+ * starting vectors (e.g. Gaussian; they must be independent on the operator's
+ * sites), on return orthonormal eigenvectors (odd sites zero for COLA_OP_EO).
+ * evals: host [nev], ascending.  Converged when every
+ * |A v_j - lambda_j v_j| <= tol lambda_j; COLA_ERR_NOT_CONVERGED after
+ * max_sweeps sweeps (the best estimates are returned).  Uses the handle's
+ * workspace block that cola_multishift_solve also uses. */
+typedef struct {
+    int nev;         /* eigenpairs wanted, 1..64 */
+    int op;          /* COLA_OP_EO or COLA_OP_FULL */
+    double tol;      /* relative residual target */
+    int max_sweeps;  /* sweeps (each: nev Ritz minimisations + one Rayleigh-Ritz step) */
+    int max_cg;      /* CG steps per vector per sweep */
+    double gamma;    /* a vector's minimisation stops once |gradient| fell by this factor */
+} cola_eig_params;
+
+typedef struct {
+    int sweeps;
+    int applications;     /* operator applications */
+    double max_rel_resid; /* max_j |A v_j - lambda_j v_j| / lambda_j at return */
+    double seconds;
+    int status;
+} cola_eig_info;
+
+cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *evals, const cola_eig_params *params,
+                            cola_eig_info *info, cudaStream_t stream);
+
 /* Fermion force of S = phi^dag (D^dag D)^-1 phi given X = (D^dag D)^-1 phi and
  * Y = D X (canonical FP64, device).  Output force_dev: real FP64 [4][V][8],
  * F^a_mu(x) = dS/d eps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x), T^a = lambda^a/2:

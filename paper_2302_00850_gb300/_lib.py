@@ -61,6 +61,16 @@ class HmcInfo(ctypes.Structure):
                 ("cg_iters", ctypes.c_int), ("seconds", ctypes.c_double)]
 
 
+class EigParams(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("op", ctypes.c_int), ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("gamma", ctypes.c_double)]
+
+
+class EigInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("applications", ctypes.c_int), ("max_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
@@ -86,6 +96,8 @@ SIGNATURES = {
                                      ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "cola_multishift_solve": (_st, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _i, _d,
                                      ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
+    "cola_eig_lowest": (_st, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(EigParams),
+                               ctypes.POINTER(EigInfo), _vp]),
     "cola_fermion_force": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_dirac_link_grad": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cola_plaquette": (_st, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),

@@ -269,6 +269,35 @@ def multishift_solve(g: Gauge, b: torch.Tensor, shifts, tol=1e-10, max_iter=1000
     return x, res
 
 
+@dataclass
+class EigInfo:
+    sweeps: int
+    applications: int
+    max_rel_resid: float
+    seconds: float
+    status: int
+
+
+def eig_lowest(g: Gauge, v0: torch.Tensor, op="eo", tol=1e-8, max_sweeps=50, max_cg=40, gamma=0.1,
+               raise_on_error=True):
+    """Lowest eigenpairs of Mhat^dag Mhat ("eo") or D^dag D ("full") (see cola_eig_lowest).
+
+    v0: starting vectors, complex128 [nev, Lt, Lz, Ly, Lx, 4, 3] (e.g. Gaussian).
+    Returns (eigenvalues float64 [nev], eigenvectors like v0, EigInfo).
+    """
+    nev = v0.shape[0]
+    vecs = v0.detach().clone().contiguous()
+    _complex_field(vecs, nev * g.volume * 12, "v0")
+    vals = (ctypes.c_double * nev)()
+    prm = _lib.EigParams(int(nev), OPS[op], float(tol), int(max_sweeps), int(max_cg), float(gamma))
+    info = _lib.EigInfo()
+    st = g.lib.cola_eig_lowest(g.handle, _ptr(vecs), vals, ctypes.byref(prm), ctypes.byref(info), _stream(g.device))
+    if st != 0 and (raise_on_error or st != -4):
+        check(st)
+    return (torch.tensor(list(vals), dtype=torch.float64), vecs,
+            EigInfo(info.sweeps, info.applications, info.max_rel_resid, info.seconds, info.status))
+
+
 def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
     """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X."""
     lx, ly, lz, lt = g.dims
