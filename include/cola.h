@@ -236,15 +236,19 @@ cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const void *b_dev, 
  * each vector minimises the Ritz functional <x, A x> / <x, x> by CG in the
  * complement of the ones before it, and every sweep ends with a
  * Rayleigh-Ritz diagonalisation of A on the span of all nev vectors.  FP64.
- * evecs_dev: canonical FP64 [nev][V][4][3] (device); on entry the caller's
- * starting vectors (e.g. Gaussian; they must be independent on the operator's
- * sites), on return orthonormal eigenvectors (odd sites zero for COLA_OP_EO).
- * evals: host [nev], ascending.  Converged when every
- * |A v_j - lambda_j v_j| <= tol lambda_j; COLA_ERR_NOT_CONVERGED after
- * max_sweeps sweeps (the best estimates are returned).  Uses the handle's
- * workspace block that cola_multishift_solve also uses. */
+ * nextra guard vectors are iterated with the nev wanted ones but not tested
+ * for convergence (they speed up levels close to the edge of the wanted set).
+ * evecs_dev: canonical FP64 [nev + nextra][V][4][3] (device); on entry the
+ * caller's starting vectors (e.g. Gaussian; they must be independent on the
+ * operator's sites), on return orthonormal Ritz vectors, the first nev the
+ * eigenvectors (odd sites zero for COLA_OP_EO).  evals: host [nev + nextra],
+ * ascending.  Converged when every |A v_j - lambda_j v_j| <= tol lambda_j
+ * for j < nev; COLA_ERR_NOT_CONVERGED after max_sweeps sweeps (the best
+ * estimates are returned).  Uses the handle's workspace block that
+ * cola_multishift_solve also uses. */
 typedef struct {
-    int nev;         /* eigenpairs wanted, 1..64 */
+    int nev;         /* eigenpairs wanted (>= 1) */
+    int nextra;      /* guard vectors (>= 0); nev + nextra <= 64 */
     int op;          /* COLA_OP_EO or COLA_OP_FULL */
     double tol;      /* relative residual target */
     int max_sweeps;  /* sweeps (each: nev Ritz minimisations + one Rayleigh-Ritz step) */

@@ -62,7 +62,8 @@ class HmcInfo(ctypes.Structure):
 
 
 class EigParams(ctypes.Structure):
-    _fields_ = [("nev", ctypes.c_int), ("op", ctypes.c_int), ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
+    _fields_ = [("nev", ctypes.c_int), ("nextra", ctypes.c_int), ("op", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("gamma", ctypes.c_double)]
 
 

@@ -278,23 +278,25 @@ class EigInfo:
     status: int
 
 
-def eig_lowest(g: Gauge, v0: torch.Tensor, op="eo", tol=1e-8, max_sweeps=50, max_cg=40, gamma=0.1,
-               raise_on_error=True):
+def eig_lowest(g: Gauge, v0: torch.Tensor, nev: int | None = None, op="eo", tol=1e-8, max_sweeps=50, max_cg=40,
+               gamma=0.1, raise_on_error=True):
     """Lowest eigenpairs of Mhat^dag Mhat ("eo") or D^dag D ("full") (see cola_eig_lowest).
 
-    v0: starting vectors, complex128 [nev, Lt, Lz, Ly, Lx, 4, 3] (e.g. Gaussian).
-    Returns (eigenvalues float64 [nev], eigenvectors like v0, EigInfo).
+    v0: starting vectors, complex128 [nev + nextra, Lt, Lz, Ly, Lx, 4, 3] (e.g.
+    Gaussian); rows beyond nev (default: all rows) are guard vectors.
+    Returns (eigenvalues float64 [nev], eigenvectors [nev, ...], EigInfo).
     """
-    nev = v0.shape[0]
+    nvec = v0.shape[0]
+    nev = nvec if nev is None else int(nev)
     vecs = v0.detach().clone().contiguous()
-    _complex_field(vecs, nev * g.volume * 12, "v0")
-    vals = (ctypes.c_double * nev)()
-    prm = _lib.EigParams(int(nev), OPS[op], float(tol), int(max_sweeps), int(max_cg), float(gamma))
+    _complex_field(vecs, nvec * g.volume * 12, "v0")
+    vals = (ctypes.c_double * nvec)()
+    prm = _lib.EigParams(nev, nvec - nev, OPS[op], float(tol), int(max_sweeps), int(max_cg), float(gamma))
     info = _lib.EigInfo()
     st = g.lib.cola_eig_lowest(g.handle, _ptr(vecs), vals, ctypes.byref(prm), ctypes.byref(info), _stream(g.device))
     if st != 0 and (raise_on_error or st != -4):
         check(st)
-    return (torch.tensor(list(vals), dtype=torch.float64), vecs,
+    return (torch.tensor(list(vals)[:nev], dtype=torch.float64), vecs[:nev],
             EigInfo(info.sweeps, info.applications, info.max_rel_resid, info.seconds, info.status))
 
 

@@ -88,11 +88,11 @@ def test_free_field_closed_form(cola):
 
 
 def test_near_degenerate_pair_on_ragged_lattice(cola):
-    """The two lowest levels here are 4e-4 apart (relative): resolved by Rayleigh-Ritz on three vectors."""
+    """The two lowest levels here are 4e-4 apart (relative): resolved by Rayleigh-Ritz (3 wanted + 2 guards)."""
     dims = (6, 4, 2, 8)
     u = synth.gauge_field(dims, 0.3, synth.seed_for(100, 3))
     g = cola.Gauge(to_dev(u), dims, KAPPA, BC_AP, precisions=("f64",))
-    vals, vecs, info = cola.eig_lowest(g, start(dims, 3, 4), op="eo", tol=1e-10)
+    vals, vecs, info = cola.eig_lowest(g, start(dims, 5, 4), nev=3, op="eo", tol=1e-10)
     apply_a, mask = op_of(u, dims, "eo")
     want, _ = oeig.lowest_dense(apply_a, dims[::-1] + (4, 3), 3, mask=mask)
     assert (want[1] - want[0]) / want[0] < 1e-3

@@ -148,11 +148,11 @@ def test_eig_parameter_errors_before_any_cuda_call(lib):
     fake = ctypes.c_void_p(1)
     vals = (ctypes.c_double * 4)()
     info = _lib.EigInfo()
-    for kw in [dict(nev=0), dict(nev=65), dict(op=3), dict(tol=0.0), dict(max_sweeps=0), dict(max_cg=0),
-               dict(gamma=1.0)]:
-        p = dict(nev=4, op=1, tol=1e-8, max_sweeps=5, max_cg=10, gamma=0.1)
+    for kw in [dict(nev=0), dict(nev=65), dict(nev=60, nextra=5), dict(nextra=-1), dict(op=3), dict(tol=0.0),
+               dict(max_sweeps=0), dict(max_cg=0), dict(gamma=1.0)]:
+        p = dict(nev=4, nextra=0, op=1, tol=1e-8, max_sweeps=5, max_cg=10, gamma=0.1)
         p.update(kw)
-        prm = _lib.EigParams(p["nev"], p["op"], p["tol"], p["max_sweeps"], p["max_cg"], p["gamma"])
+        prm = _lib.EigParams(p["nev"], p["nextra"], p["op"], p["tol"], p["max_sweeps"], p["max_cg"], p["gamma"])
         assert lib.cola_eig_lowest(fake, fake, vals, ctypes.byref(prm), ctypes.byref(info), None) == -1, kw
     assert lib.cola_eig_lowest(None, fake, vals, None, ctypes.byref(info), None) == -1
 
