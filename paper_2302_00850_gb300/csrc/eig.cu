@@ -330,7 +330,10 @@ cola_status normalize(Ctx &c, char *x) {
     return comb(c, x, {{x, cplx(1.0 / std::sqrt(d[0].x))}});
 }
 
-// Ritz-functional CG for v_j over the complement of v_0 .. v_{j-1}
+// Ritz-functional CG for v_j over the complement of v_0 .. v_{j-1}.  Three
+// host reads per step: {<x, p>, |p|^2}, {<x, A p>, <p, A p>} and
+// {<v_i, g> (i < j), |g|^2, <x, p>}; the norms after a projection follow from
+// those (|p - <x,p> x|^2 = |p|^2 - |<x,p>|^2 for unit x, and likewise for g).
 cola_status ritz_cg(Ctx &c, int j, int max_cg, double gamma, double tol) {
     char *x = c.V[j], *y = c.x_y, *g = c.g_, *p = c.p, *z = c.z;
     EIG_TRY(project(c, x, j));
@@ -339,41 +342,58 @@ cola_status ritz_cg(Ctx &c, int j, int max_cg, double gamma, double tol) {
     std::vector<double2> d;
     EIG_TRY(dots(c, {{x, y}}, d));
     double mu = d[0].x;
-    EIG_TRY(comb(c, g, {{y, cplx(1.0)}, {x, cplx(-mu)}}));
-    EIG_TRY(project(c, g, j));
-    EIG_TRY(dots(c, {{g, g}}, d));
-    const double gg0 = d[0].x;
+    // g = Q (y - mu x), one classical Gram-Schmidt pass
+    auto gradient = [&](double &gg, double2 *xp) -> cola_status {
+        EIG_TRY(comb(c, g, {{y, cplx(1.0)}, {x, cplx(-mu)}}));
+        std::vector<std::pair<const char *, const char *>> ab;
+        for (int i = 0; i < j; ++i) ab.push_back({c.V[i], g});
+        ab.push_back({g, g});
+        if (xp) ab.push_back({x, p});
+        EIG_TRY(dots(c, ab, d));
+        double n2 = d[j].x;
+        if (j > 0) {
+            std::vector<std::pair<const char *, double2>> t = {{g, cplx(1.0)}};
+            for (int i = 0; i < j; ++i) {
+                t.push_back({c.V[i], cplx(-d[i].x, -d[i].y)});
+                n2 -= d[i].x * d[i].x + d[i].y * d[i].y;
+            }
+            EIG_TRY(comb(c, g, t));
+        }
+        gg = std::max(n2, 0.0);
+        if (xp) *xp = d[j + 1];
+        return COLA_OK;
+    };
+    double gg0 = 0.0;
+    EIG_TRY(gradient(gg0, nullptr));
     double gg = gg0;
     EIG_CUDA(cudaMemcpyAsync(p, g, c.fb, cudaMemcpyDeviceToDevice, c.s), "p = g");
     for (int k = 0; k < max_cg; ++k) {
         if (gg <= gamma * gamma * gg0 || std::sqrt(gg) <= 0.1 * tol * std::fabs(mu) || gg == 0.0) break;
-        // keep p orthogonal to x
-        EIG_TRY(dots(c, {{x, p}}, d));
-        EIG_TRY(comb(c, p, {{p, cplx(1.0)}, {x, cplx(-d[0].x, -d[0].y)}}));
-        EIG_TRY(dots(c, {{p, p}}, d));
-        const double pn = std::sqrt(d[0].x);
-        if (!(pn > 0.0)) break;
-        EIG_TRY(comb(c, p, {{p, cplx(1.0 / pn)}}));  // p^
-        EIG_TRY(apply_a(c, z, p));
+        // p <- p - <x, p> x (keep p orthogonal to x)
+        EIG_TRY(dots(c, {{x, p}, {p, p}}, d));
+        const double2 xp = d[0];
+        const double pn2 = d[1].x - (xp.x * xp.x + xp.y * xp.y);
+        if (!(pn2 > 0.0)) break;
+        EIG_TRY(comb(c, p, {{p, cplx(1.0)}, {x, cplx(-xp.x, -xp.y)}}));
+        const double pn = std::sqrt(pn2);
+        EIG_TRY(apply_a(c, z, p));  // z = A p = pn A p^
         EIG_TRY(dots(c, {{x, z}, {p, z}}, d));
-        const double a = mu, b = d[0].x, cc = d[1].x;
+        const double a = mu, b = d[0].x / pn, cc = d[1].x / pn2;
         const double h = 0.5 * (a - cc), R = std::sqrt(h * h + b * b);
         if (!(R > 0.0)) break;
         // cos 2t = -h / R, sin 2t = -b / R; half angle with cos t >= 0
         const double c2 = -h / R, s2 = -b / R;
         const double ct = std::sqrt(std::max(0.0, 0.5 * (1.0 + c2)));
         const double st = ct > 1e-8 ? s2 / (2.0 * ct) : (s2 >= 0.0 ? 1.0 : -1.0) * std::sqrt(std::max(0.0, 0.5 * (1.0 - c2)));
-        EIG_TRY(comb(c, x, {{x, cplx(ct)}, {p, cplx(st)}}));
-        EIG_TRY(comb(c, y, {{y, cplx(ct)}, {z, cplx(st)}}));
+        EIG_TRY(comb(c, x, {{x, cplx(ct)}, {p, cplx(st / pn)}}));
+        EIG_TRY(comb(c, y, {{y, cplx(ct)}, {z, cplx(st / pn)}}));
         mu = 0.5 * (a + cc) - R;
-        // gradient of the new point
-        EIG_TRY(comb(c, g, {{y, cplx(1.0)}, {x, cplx(-mu)}}));
-        EIG_TRY(project(c, g, j));
-        EIG_TRY(dots(c, {{g, g}, {x, p}}, d));
-        const double gg_new = d[0].x;
+        double gg_new = 0.0;
+        double2 xpn;
+        EIG_TRY(gradient(gg_new, &xpn));  // also <x', p>
         const double beta = gg_new / gg;
-        // p = g + beta (p^ pn - <x, p^ pn> x): restore |p| before the recurrence
-        EIG_TRY(comb(c, p, {{g, cplx(1.0)}, {p, cplx(beta * pn)}, {x, cplx(-beta * pn * d[1].x, -beta * pn * d[1].y)}}));
+        // p = g' + beta (p - <x', p> x')
+        EIG_TRY(comb(c, p, {{g, cplx(1.0)}, {p, cplx(beta)}, {x, cplx(-beta * xpn.x, -beta * xpn.y)}}));
         gg = gg_new;
     }
     return normalize(c, x);
