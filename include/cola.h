@@ -13,7 +13,12 @@
  * gamma matrices in the Hermitian chiral (DeGrand-Rossi) basis, Ut_mu(x) =
  * U_mu(x) * bc[mu] on links that cross the lattice boundary (x_mu = L_mu - 1).
  * Even-odd preconditioning uses the Schur operator on even sites,
- * Mhat = 1 - kappa^2 H_eo H_oe, whose determinant equals det D.
+ * Mhat = 1 - kappa^2 H_eo H_oe, whose determinant equals det D.  A handle may
+ * carry a clover term A(x) (cola_clover_attach): then D = A - kappa H and
+ * Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe.  Around the operator: CG solves
+ * (plain FP64 or mixed precision, many right-hand sides, batches of
+ * lattices), multi-shift CG, the fermion and gauge forces and an HMC
+ * trajectory driver, and a Kalkreuter-Simma eigensolver.
  *
  * Conventions shared by every call:
  *  - Site index i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
@@ -26,10 +31,14 @@
  *    side cola_spinor_bytes(lat, prec, 1) bytes, right-hand side outermost.
  *  - Every pointer is a DEVICE pointer unless its comment says host.  The
  *    caller owns every buffer it passes; the library owns only what a handle
- *    holds (packed links, solver workspace), released by cola_gauge_destroy.
+ *    holds (packed links, clover fields, solver workspace), released by
+ *    cola_gauge_destroy.
  *  - All work is ordered on the given stream; calls return after enqueuing,
- *    except cola_cg_solve*, which synchronise the stream once at the end to
- *    fill their info structs.
+ *    except those that report results to the host (the solvers, the
+ *    eigensolver, the HMC trajectory, cola_plaquette, cola_clover_attach),
+ *    which synchronise the stream.
+ *  - A handle is not thread-safe: its workspace is reused by every call, so
+ *    calls on one handle must be ordered (one stream, or synchronised).
  *  - Errors are returned as cola_status codes; nothing aborts.  The message
  *    of the last failure on the calling thread is cola_last_error().
  */
