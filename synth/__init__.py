@@ -174,3 +174,73 @@ def su3_direction(dims, seed: int) -> np.ndarray:
     _check_dims(dims)
     lx, ly, lz, lt = dims
     return normals(seed, 4 * lattice_volume(dims) * 8).reshape(4, lt, lz, ly, lx, 8)
+
+
+# ------------------------------------------------------------------ device --
+# The same SplitMix64 / Box-Muller recipe evaluated with torch on a device,
+# in chunks, for lattices whose inputs would take minutes on the host.  The
+# integer stream is bit-identical to the host one (64-bit wrap-around
+# multiplication; logical shifts emulated by masking the arithmetic ones); the
+# normals agree with the host ones to rounding (a different log / cos / sin).
+
+def _device_uniforms(seed: int, start: int, count: int, device):
+    import torch
+
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+
+    def as_i64(v):
+        v &= (1 << 64) - 1
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    def lshr(z, k):  # logical right shift of the 64-bit pattern
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    z = as_i64(seed) + idx * as_i64(int(GOLDEN))
+    z = (z ^ lshr(z, 30)) * as_i64(int(_M1))
+    z = (z ^ lshr(z, 27)) * as_i64(int(_M2))
+    z = z ^ lshr(z, 31)
+    return lshr(z, 11).to(torch.float64) * (2.0 ** -53)
+
+
+def _device_normals(seed: int, start_pair: int, npairs: int, device):
+    import torch
+
+    u = _device_uniforms(seed, 2 * start_pair, 2 * npairs, device).reshape(npairs, 2)
+    r = torch.sqrt(-2.0 * torch.log1p(-u[:, 0]))
+    th = 2.0 * np.pi * u[:, 1]
+    return torch.stack([r * torch.cos(th), r * torch.sin(th)], dim=1).reshape(-1)
+
+
+def gauge_field_device(dims, eps: float, seed: int, device="cuda", chunk: int = 1 << 22):
+    """gauge_field computed on `device` in chunks of `chunk` links: a torch
+    complex128 tensor [4, Lt, Lz, Ly, Lx, 3, 3] (same draw order and recipe)."""
+    import torch
+
+    _check_dims(dims)
+    lx, ly, lz, lt = dims
+    n = lattice_volume(dims) * 4
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    eye = torch.eye(3, dtype=torch.complex128, device=device)
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        g = _device_normals(seed, s * 9, m * 9, device) * np.sqrt(0.5)  # 18 normals (9 pairs) per matrix
+        a = torch.complex(g[0::2], g[1::2]).reshape(m, 3, 3)
+        h = 0.5 * (a + a.conj().transpose(-1, -2))
+        h = h - (torch.diagonal(h, dim1=-2, dim2=-1).sum(-1) / 3.0)[:, None, None] * eye
+        out[s:s + m] = _reunitarise(torch.linalg.matrix_exp(1j * eps * h))
+    return out.reshape(lt, lz, ly, lx, 4, 3, 3).permute(4, 0, 1, 2, 3, 5, 6).contiguous()
+
+
+def gaussian_spinor_device(dims, seed: int, device="cuda", chunk: int = 1 << 24):
+    """gaussian_spinor computed on `device` (same draw order and recipe)."""
+    import torch
+
+    _check_dims(dims)
+    lx, ly, lz, lt = dims
+    n = lattice_volume(dims) * 12  # complex numbers = normal pairs
+    out = torch.empty(n, dtype=torch.complex128, device=device)
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        g = _device_normals(seed, s, m, device) * np.sqrt(0.5)
+        out[s:s + m] = torch.complex(g[0::2], g[1::2])
+    return out.reshape(lt, lz, ly, lx, 4, 3)

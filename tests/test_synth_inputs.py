@@ -36,3 +36,18 @@ def test_point_sources():
     assert s.shape == (12, 4, 4, 4, 4, 4, 3)
     assert np.all(np.sum(np.abs(s), axis=(1, 2, 3, 4, 5, 6)) == 1)
     assert s[5, 0, 0, 0, 0, 1, 2] == 1
+
+
+def test_device_generators_follow_the_host_recipe():
+    """The chunked torch path (run here on the CPU device) draws the same stream."""
+    import torch  # noqa: F401
+
+    seed = synth.seed_for(6, 1)
+    assert np.array_equal(synth.uniforms(seed, 10, 1000), synth._device_uniforms(seed, 10, 1000, "cpu").numpy())
+    dims = (4, 4, 2, 4)
+    s_host = synth.gaussian_spinor(dims, seed)
+    s_dev = synth.gaussian_spinor_device(dims, seed, device="cpu", chunk=100).numpy()
+    assert np.max(np.abs(s_host - s_dev)) < 1e-15
+    u_host = synth.gauge_field(dims, 0.3, seed)
+    u_dev = synth.gauge_field_device(dims, 0.3, seed, device="cpu", chunk=7).numpy()
+    assert np.max(np.abs(u_host - u_dev)) < 1e-15
