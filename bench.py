@@ -311,9 +311,10 @@ def run_cola(args):
     ds32_gbs = BYTES_PER_SITE_F32 * vh / (ds32_us * 1e-6) / 1e9
     del g32, p32, t32
 
-    # the sections beside the headline: a failure is reported in its place, never fatal
+    # the sections beside the headline: a failure is reported in its place, never
+    # fatal; they run in single-process runs only (a replica run measures the headline)
     def section(skip, fn, *a):
-        if skip:
+        if skip or world > 1:
             return None
         try:
             return fn(*a)
