@@ -1,14 +1,38 @@
 // C ABI entry points: argument checks, gauge handles, workspace, and the
 // operator compositions (D, Mhat, their normal operators) built from the
 // hopping kernel.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
 #include "cola_impl.h"
 
 namespace cola {
+
+bool log_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("COLA_LOG");
+        return e && e[0] && e[0] != '0';
+    }();
+    return on;
+}
+
+void log_line(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "cola: %s\n", buf);
+}
+
+TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 static thread_local std::string g_last_error;
 
@@ -240,6 +264,7 @@ size_t cola_spinor_bytes(const cola_lattice *lat, cola_prec prec, int nrhs) {
 
 cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev, const cola_gauge_opts *opts,
                               cudaStream_t stream, cola_gauge *out) {
+    TraceRange trace_("cola_gauge_create");
     COLA_TRY(check_lattice(lat));
     if (!links_dev || !opts || !out) return arg_error("null argument to cola_gauge_create");
     if ((opts->prec_mask & 7u) == 0 || (opts->prec_mask & ~7u))
@@ -269,6 +294,7 @@ cola_status cola_gauge_create(const cola_lattice *lat, const void *links_dev, co
 }
 
 cola_status cola_gauge_update(cola_gauge g, const void *links_dev, cudaStream_t stream) {
+    TraceRange trace_("cola_gauge_update");
     if (!g || !links_dev) return arg_error("null argument to cola_gauge_update");
     for (int p = 0; p < 3; ++p)
         if (g->links[p])
@@ -279,6 +305,7 @@ cola_status cola_gauge_update(cola_gauge g, const void *links_dev, cudaStream_t 
 }
 
 cola_status cola_clover_attach(cola_gauge g, double csw, cudaStream_t stream) {
+    TraceRange trace_("cola_clover_attach");
     if (!g) return arg_error("null gauge handle");
     if (!std::isfinite(csw)) return arg_error("c_sw is not finite");
     if (csw == 0.0) {
@@ -301,6 +328,7 @@ double cola_clover_csw(cola_gauge g) { return g ? g->csw : 0.0; }
 
 cola_status cola_clover_apply(cola_gauge g, void *out, const void *in, int parity, int inverse, cola_prec prec,
                               int nrhs, cudaStream_t stream) {
+    TraceRange trace_("cola_clover_apply");
     if (!g || !out || !in) return arg_error("null argument to cola_clover_apply");
     if (parity < 0 || parity > 2) return arg_error("parity must be 0, 1 or 2");
     COLA_TRY(check_prec(g, prec));
@@ -333,6 +361,7 @@ cola_status cola_gauge_destroy(cola_gauge g) {
 
 cola_status cola_spinor_pack(cola_gauge g, void *packed_dev, const void *canon_dev, cola_prec prec, int nrhs,
                              cudaStream_t stream) {
+    TraceRange trace_("cola_spinor_pack");
     if (!g || !packed_dev || !canon_dev) return arg_error("null argument to cola_spinor_pack");
     if (prec < 0 || prec > 2) return arg_error("bad precision");
     COLA_TRY(check_rhs(nrhs));
@@ -341,6 +370,7 @@ cola_status cola_spinor_pack(cola_gauge g, void *packed_dev, const void *canon_d
 
 cola_status cola_spinor_unpack(cola_gauge g, void *canon_dev, const void *packed_dev, cola_prec prec, int nrhs,
                                cudaStream_t stream) {
+    TraceRange trace_("cola_spinor_unpack");
     if (!g || !packed_dev || !canon_dev) return arg_error("null argument to cola_spinor_unpack");
     if (prec < 0 || prec > 2) return arg_error("bad precision");
     COLA_TRY(check_rhs(nrhs));
@@ -350,6 +380,7 @@ cola_status cola_spinor_unpack(cola_gauge g, void *canon_dev, const void *packed
 
 cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const void *in_self, double a, double b,
                               int parity, int dagger, cola_prec prec, int nrhs, cudaStream_t stream) {
+    TraceRange trace_("cola_dslash_apply");
     if (!g || !out || !in) return arg_error("null argument to cola_dslash_apply");
     if (parity < 0 || parity > 2) return arg_error("parity must be 0, 1 or 2");
     if (a != 0.0 && !in_self) return arg_error("in_self is null but a != 0");
@@ -363,6 +394,7 @@ cola_status cola_dslash_apply(cola_gauge g, void *out, const void *in, const voi
 
 cola_status cola_dirac_apply(cola_gauge g, void *out, const void *in, int dagger, cola_prec prec, int nrhs,
                              cudaStream_t stream) {
+    TraceRange trace_("cola_dirac_apply");
     if (!g || !out || !in) return arg_error("null argument to cola_dirac_apply");
     if (out == in) return arg_error("out must not alias in");
     COLA_TRY(check_prec(g, prec));
@@ -374,6 +406,7 @@ cola_status cola_dirac_apply(cola_gauge g, void *out, const void *in, int dagger
 
 cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, cola_prec prec, int nrhs,
                              cudaStream_t stream) {
+    TraceRange trace_("cola_mdagm_apply");
     if (!g || !out || !in) return arg_error("null argument to cola_mdagm_apply");
     if (op != COLA_OP_FULL && op != COLA_OP_EO) return arg_error("op must be COLA_OP_FULL or COLA_OP_EO");
     if (out == in) return arg_error("out must not alias in");
@@ -388,6 +421,7 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
 
 cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_dev, const void *Y_dev,
                                cudaStream_t stream) {
+    TraceRange trace_("cola_fermion_force");
     if (!g || !force_dev || !X_dev || !Y_dev) return arg_error("null argument to cola_fermion_force");
     COLA_TRY(check_prec(g, COLA_F64));
     if (g->csw != 0.0) return clover_unsupported("cola_fermion_force");
@@ -398,6 +432,7 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
 
 cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev, const void *gy_dev,
                                  cudaStream_t stream) {
+    TraceRange trace_("cola_dirac_link_grad");
     if (!g || !grad_links_dev || !psi_dev || !gy_dev) return arg_error("null argument to cola_dirac_link_grad");
     if (g->csw != 0.0) return clover_unsupported("cola_dirac_link_grad");
     return cuda_check(launch_link_grad(g->geom, g->lat.kappa, grad_links_dev, psi_dev, gy_dev, stream),

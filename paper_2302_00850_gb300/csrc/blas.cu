@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(kBlasBlock) norm2_kernel(const __grid_constant
 // ------------------------------------------------------------- finishing --
 enum FinishMode { FIN_XR, FIN_PQ, FIN_RU, FIN_NORM, FIN_INIT };
 
+// reliable updates without a new smallest true residual before a row stops
+constexpr int kStallUpdates = 3;
+
 // One block per row: sum the row's block partials in block order, then decide.
 template <int MODE>
 __global__ void __launch_bounds__(512) finish_kernel(const __grid_constant__ BlasArgs B) {
@@ -281,13 +284,21 @@ __global__ void __launch_bounds__(512) finish_kernel(const __grid_constant__ Bla
             S.r2_last = tot;
             S.ru = 0;
             S.ru_count += 1;
+            // stagnation: the FP64 true residual has not improved over kStallUpdates
+            // reliable updates (a tolerance below what the precision reaches)
+            if (S.r2_best == 0.0 || tot < S.r2_best) {
+                S.r2_best = tot;
+                S.stall = 0;
+            } else {
+                S.stall += 1;
+            }
             if (!isfinite(tot)) {
                 S.status = COLA_ERR_BREAKDOWN;
                 S.done = 1;
             } else if (tot <= S.tol2) {
                 S.status = COLA_OK;
                 S.done = 1;
-            } else if (S.iter >= S.max_iter) {
+            } else if (S.iter >= S.max_iter || S.stall >= kStallUpdates) {
                 S.status = COLA_ERR_NOT_CONVERGED;
                 S.done = 1;
             }

@@ -245,4 +245,14 @@ cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nr
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
                         CgState *st, bool filter_ru, cudaStream_t s);
 cola_status cuda_check(cudaError_t e, const char *what);
+
+// COLA_LOG=1 in the environment: one line per solve / eigensolve / trajectory on stderr
+bool log_enabled();
+void log_line(const char *fmt, ...);
+
+// Named range for profilers and tracers (NVTX; no cost without a tool attached).
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+};
 }  // namespace cola

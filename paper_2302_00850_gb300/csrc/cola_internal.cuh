@@ -552,6 +552,8 @@ struct CgState {
     double tol2;     // tol^2 |b|^2
     double delta2;   // delta^2
     double shift;    // sigma: this row solves (A + sigma) x = b
+    double r2_best;  // smallest FP64 true |r|^2 so far (0: none yet)
+    int stall;       // reliable updates since r2_best last improved
     int iter;
     int max_iter;
     int ru;          // a reliable update is due

@@ -411,6 +411,7 @@ using namespace cola;
 
 extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *evals, const cola_eig_params *prm,
                                        cola_eig_info *info, cudaStream_t s) {
+    TraceRange trace_("cola_eig_lowest");
     const auto t0 = std::chrono::steady_clock::now();
     if (!g || !evecs_dev || !evals || !prm || !info) return arg_error("null argument to cola_eig_lowest");
     if (prm->nev < 1 || prm->nextra < 0 || prm->nev + prm->nextra > kMaxNev)
@@ -544,6 +545,9 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
     info->max_rel_resid = worst;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     info->status = converged ? COLA_OK : COLA_ERR_NOT_CONVERGED;
+    if (log_enabled())
+        log_line("eig_lowest: status %d, %d sweeps, %d operator applications, lambda_0 %.6e, max relative residual "
+                 "%.3e, %.3f s", info->status, info->sweeps, info->applications, lam[0], worst, info->seconds);
     if (!converged) set_error("eigensolver did not converge within max_sweeps");
     return (cola_status)info->status;
 }

@@ -210,6 +210,7 @@ using namespace cola;
 extern "C" {
 
 cola_status cola_plaquette(cola_gauge g, double *plaq, cudaStream_t stream) {
+    TraceRange trace_("cola_plaquette");
     if (!g || !plaq) return arg_error("null argument to cola_plaquette");
     HMC_TRY(need_f64(g));
     double *scratch, *res;
@@ -222,6 +223,7 @@ cola_status cola_plaquette(cola_gauge g, double *plaq, cudaStream_t stream) {
 }
 
 cola_status cola_gauge_force(cola_gauge g, double beta, double *force_dev, cudaStream_t stream) {
+    TraceRange trace_("cola_gauge_force");
     if (!g || !force_dev) return arg_error("null argument to cola_gauge_force");
     if (!std::isfinite(beta)) return arg_error("beta is not finite");
     HMC_TRY(need_f64(g));
@@ -231,6 +233,7 @@ cola_status cola_gauge_force(cola_gauge g, double beta, double *force_dev, cudaS
 }
 
 cola_status cola_link_update(cola_gauge g, void *links_dev, const double *mom_dev, double eps, cudaStream_t stream) {
+    TraceRange trace_("cola_link_update");
     if (!g || !links_dev || !mom_dev) return arg_error("null argument to cola_link_update");
     if (!std::isfinite(eps)) return arg_error("eps is not finite");
     HMC_CUDA(launch_link_update(g->geom, links_dev, mom_dev, eps, stream), "link update");
@@ -239,6 +242,7 @@ cola_status cola_link_update(cola_gauge g, void *links_dev, const double *mom_de
 
 cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, const void *eta_dev,
                                 const cola_hmc_params *params, cola_hmc_info *info, cudaStream_t stream) {
+    TraceRange trace_("cola_hmc_trajectory");
     if (!g || !links_dev || !mom_dev || !params || !info) return arg_error("null argument to cola_hmc_trajectory");
     HMC_TRY(check_hmc_params(params));
     HMC_TRY(need_f64(g));
@@ -294,6 +298,9 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
     info->force_evals = T.force_evals;
     info->cg_iters = T.cg_iters;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (log_enabled())
+        log_line("hmc_trajectory: dH %.6e (%s), plaquette %.6f, %d force evaluations, %d CG iterations, %.3f s", dh,
+                 accept ? "accepted" : "rejected", plaq, T.force_evals, T.cg_iters, info->seconds);
     return COLA_OK;
 }
 

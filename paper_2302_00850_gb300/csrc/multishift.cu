@@ -322,6 +322,7 @@ using namespace cola;
 extern "C" cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const void *b_dev, const double *shifts,
                                              int nshift, double tol_sloppy, const cola_solver_params *prm,
                                              cola_solve_info *info, cudaStream_t s) {
+    TraceRange trace_("cola_multishift_solve");
     const auto t0 = std::chrono::steady_clock::now();
     if (!g || !x_dev || !b_dev || !shifts || !prm || !info) return arg_error("null argument to cola_multishift_solve");
     if (nshift < 1 || nshift > kMaxShifts) return arg_error("nshift must be in 1..64");
@@ -442,6 +443,10 @@ extern "C" cola_status cola_multishift_solve(cola_gauge g, void *x_dev, const vo
         info[i] = inf[i];
         info[i].iters += cur.sh[i].iters;
         info[i].seconds = secs;
+        if (log_enabled())
+            log_line("multishift shift %d (sigma %.4g): status %d, %d iterations (%d in the recurrence), true residual "
+                     "%.3e, %.3f s", i, shifts[i], info[i].status, info[i].iters, cur.sh[i].iters,
+                     info[i].true_rel_resid, secs);
     }
     return st;
 }

@@ -567,8 +567,17 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
         info[r].status = st.status;
         if (st.status != COLA_OK && worst == COLA_OK) worst = (cola_status)st.status;
     }
-    if (worst != COLA_OK) set_error(worst == COLA_ERR_BREAKDOWN ? "CG breakdown (non-finite or non-positive scalar)"
-                                                                : "CG did not converge within max_iter");
+    bool stalled = false;
+    for (int r = 0; r < nrows; ++r) stalled |= hs[r].status == COLA_ERR_NOT_CONVERGED && hs[r].iter < hs[r].max_iter;
+    if (worst != COLA_OK)
+        set_error(worst == COLA_ERR_BREAKDOWN ? "CG breakdown (non-finite or non-positive scalar)"
+                  : stalled ? "CG stagnated: the FP64 true residual did not improve over 3 reliable updates "
+                              "(is the tolerance below what FP64 reaches for this operator?)"
+                            : "CG did not converge within max_iter");
+    if (log_enabled())
+        for (int r = 0; r < nrows; ++r)
+            log_line("cg_solve row %d: status %d, %d iterations, %d reliable updates, true residual %.3e, %.3f s", r,
+                     info[r].status, info[r].iters, info[r].reliable_updates, info[r].true_rel_resid, secs);
     return worst;
 }
 
@@ -585,6 +594,7 @@ using namespace cola;
 
 extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev, const cola_solver_params *prm,
                                      cola_solve_info *info, cudaStream_t s) {
+    TraceRange trace_("cola_cg_solve");
     if (!g || !x_dev || !b_dev || !prm || !info) return arg_error("null argument to cola_cg_solve");
     return solve_batch(1, &g, &x_dev, &b_dev, prm, info, s);
 }
@@ -592,6 +602,7 @@ extern "C" cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_de
 extern "C" cola_status cola_cg_solve_batched(int nlat, const cola_gauge *gauges, void *const *x_dev,
                                              const void *const *b_dev, const cola_solver_params *prm,
                                              cola_solve_info *info, cudaStream_t s) {
+    TraceRange trace_("cola_cg_solve_batched");
     if (nlat < 1 || nlat > kMaxBatch) return arg_error("nlat must be in 1..8");
     if (!gauges || !x_dev || !b_dev || !prm || !info) return arg_error("null argument to cola_cg_solve_batched");
     for (int l = 0; l < nlat; ++l)

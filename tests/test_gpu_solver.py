@@ -221,3 +221,38 @@ def test_cached_solve_graph_is_reused_and_stays_correct(cola):
     x3, i3 = cola.cg_solve(g, to_dev(b3), op="eo", inner="f16", use_graph=True)
     for r in range(2):
         assert true_resid_eo(u2, x3[r].cpu().numpy(), b3[r], kappa, dims) <= 1e-10
+
+
+@pytest.mark.parametrize("inner", ["f64", "f16"])
+def test_stagnation_is_detected(cola, inner):
+    """A tolerance below what FP64 reaches: the true residual stops improving and the
+    solver stops after three reliable updates without a new best, not at max_iter."""
+    dims = (4, 4, 4, 4)
+    u, b = lattice_inputs(dims, config=59)
+    g = cola.Gauge(to_dev(u), dims, 0.12, BC_AP, precisions=("f64", "f16"))
+    x, info = cola.cg_solve(g, to_dev(b), tol=1e-19, max_iter=100000, op="eo", inner=inner, raise_on_error=False)
+    assert info[0].status == -4
+    assert info[0].iters < 2000
+    assert info[0].true_rel_resid < 1e-13
+    with pytest.raises(cola.ColaError, match="stagnated"):
+        cola.cg_solve(g, to_dev(b), tol=1e-19, max_iter=100000, op="eo", inner=inner)
+
+
+def test_cola_log_reports_each_solve(tmp_path):
+    import os
+    import subprocess
+    import sys
+
+    code = (
+        "import torch, synth, paper_2302_00850_gb300 as cola\n"
+        "d = (4, 4, 4, 4)\n"
+        "u = torch.from_numpy(synth.gauge_field(d, 0.3, synth.seed_for(0, 0))).cuda()\n"
+        "b = torch.from_numpy(synth.gaussian_spinor(d, synth.seed_for(0, 1))).cuda()\n"
+        "g = cola.Gauge(u, d, 0.12, (1, 1, 1, -1), precisions=('f64',))\n"
+        "cola.cg_solve(g, b, tol=1e-10, op='eo')\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, COLA_LOG="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "cola: cg_solve row 0: status 0" in r.stderr
