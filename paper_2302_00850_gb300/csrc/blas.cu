@@ -230,6 +230,10 @@ enum FinishMode { FIN_XR, FIN_PQ, FIN_RU, FIN_NORM, FIN_INIT };
 
 // reliable updates without a new smallest true residual before a row stops
 constexpr int kStallUpdates = 3;
+// iterations without a 4x drop of the iterated |r|^2 before a true-residual check
+constexpr int kPlateauIters = 500;
+// (|r|/|b|)^2 below which FP64 CG checks its true residual every 100x drop of |r|
+constexpr double kDeepRel2 = 1e-28;
 
 // One block per row: sum the row's block partials in block order, then decide.
 template <int MODE>
@@ -276,7 +280,18 @@ __global__ void __launch_bounds__(512) finish_kernel(const __grid_constant__ Bla
                 S.status = COLA_ERR_BREAKDOWN;
                 S.done = 1;
             } else {
-                S.ru = (tot < S.delta2 * S.r2_last) || (tot <= S.tol2) || (S.iter >= S.max_iter);
+                // Two more triggers of an FP64 true residual, so that a solve whose
+                // tolerance is out of reach is seen to stagnate even when delta never
+                // fires (plain FP64 CG): a plateau of the iterated residual (no 4x drop
+                // in kPlateauIters iterations), and, in FP64 CG below the level FP64
+                // resolves (|r|/|b| < 1e-14), every further 100x drop of |r|.
+                if (tot < 0.25 * S.rho_mark) {
+                    S.rho_mark = tot;
+                    S.it_mark = S.iter;
+                }
+                const bool deep = S.delta2 == 0.0 && tot < kDeepRel2 * S.b2 && tot < 1e-4 * S.r2_last;
+                S.ru = (tot < S.delta2 * S.r2_last) || (tot <= S.tol2) || (S.iter >= S.max_iter) ||
+                       (S.iter - S.it_mark >= kPlateauIters) || deep;
             }
         } else {  // FIN_RU
             if (!ru_live(B, S)) return;
@@ -292,6 +307,8 @@ __global__ void __launch_bounds__(512) finish_kernel(const __grid_constant__ Bla
             } else {
                 S.stall += 1;
             }
+            S.rho_mark = tot;
+            S.it_mark = S.iter;
             if (!isfinite(tot)) {
                 S.status = COLA_ERR_BREAKDOWN;
                 S.done = 1;

@@ -553,6 +553,8 @@ struct CgState {
     double delta2;   // delta^2
     double shift;    // sigma: this row solves (A + sigma) x = b
     double r2_best;  // smallest FP64 true |r|^2 so far (0: none yet)
+    double rho_mark; // iterated |r|^2 at the last 4x drop (or the last reliable update)
+    int it_mark;     // iteration of rho_mark
     int stall;       // reliable updates since r2_best last improved
     int iter;
     int max_iter;

@@ -226,13 +226,15 @@ def test_cached_solve_graph_is_reused_and_stays_correct(cola):
 @pytest.mark.parametrize("inner", ["f64", "f16"])
 def test_stagnation_is_detected(cola, inner):
     """A tolerance below what FP64 reaches: the true residual stops improving and the
-    solver stops after three reliable updates without a new best, not at max_iter."""
+    solver stops after three reliable updates without a new best, not at max_iter
+    (for plain FP64 CG those updates come from the checks below |r|/|b| = 1e-14 and
+    on a 500-iteration plateau of the iterated residual)."""
     dims = (4, 4, 4, 4)
     u, b = lattice_inputs(dims, config=59)
     g = cola.Gauge(to_dev(u), dims, 0.12, BC_AP, precisions=("f64", "f16"))
     x, info = cola.cg_solve(g, to_dev(b), tol=1e-19, max_iter=100000, op="eo", inner=inner, raise_on_error=False)
     assert info[0].status == -4
-    assert info[0].iters < 2000
+    assert info[0].iters < 5000
     assert info[0].true_rel_resid < 1e-13
     with pytest.raises(cola.ColaError, match="stagnated"):
         cola.cg_solve(g, to_dev(b), tol=1e-19, max_iter=100000, op="eo", inner=inner)
