@@ -21,11 +21,26 @@ the phase and its conjugate).
 Even-odd: D_sw = [[A_ee, -kappa H_eo], [-kappa H_oe, A_oo]], Schur operator on
 even sites Mhat = A_ee - kappa^2 H_eo A_oo^-1 H_oe, det D_sw = det A_oo det Mhat,
 Mhat^dag = A_ee - kappa^2 H^dag_eo A_oo^-1 H^dag_oe = gamma5 Mhat gamma5.
+
+Clover force.  For S = phi^dag (D_sw^dag D_sw)^-1 phi, X = (D_sw^dag D_sw)^-1 phi
+and Y = D_sw X, dS = -2 Re Y^dag dD_sw X (force.py); the clover part is
+dA = -kappa c_sw sum sigma_mn dF_mn, so with
+  Lam_mn(x)_ba = sum_st (sigma_mn)_st X(x)_tb conj(Y(x)_sa),
+  Gam_mn(x)    = L + L^dag,  L = Lam_mn(x) - tr Lam_mn(x) / 3   (Hermitian, traceless),
+the traceless projection moves onto Lam, Re Tr[dF Lam] = Im Tr[dQ Gam] / 8, and
+  dS_clover = (kappa c_sw / 4) sum_x sum_{m<n} Im Tr[dQ_mn(x) Gam_mn(x)].
+Under U_r(y) -> (1 + i eps T^a) U_r(y), a leaf B U A (U = U_r(y)) changes by
+i eps B T U A and a leaf B U^dag A by -i eps B U^dag T A, so each factor of
+each leaf adds (kappa c_sw / 4) Re Tr[T^a U A Gam B] or
+-(kappa c_sw / 4) Re Tr[T^a A Gam B U^dag] to the link it stands for.
+clover_force_coeffs writes exactly that sum over leaves and factors.
 """
 from __future__ import annotations
 
 import numpy as np
 
+from .force import T_GEN
+from .solve import cg
 from .wilson import GAMMA, GAMMA5, hop, hop_block, parity_of_sites
 
 SIGMA = np.zeros((4, 4, 4, 4), dtype=np.complex128)
@@ -169,3 +184,72 @@ def clover_sites(u, kappa, csw, sites):
                 a -= kappa * csw * np.kron(SIGMA[mu, nu], f)
         out[n] = a.reshape(4, 3, 4, 3)
     return out
+
+
+# The four leaves of Q_mn(x) as paths of factors (d, om, on, adj): the link of
+# direction mu (d = 0) or nu (d = 1) at x + om mu + on nu, adjoint or not, in
+# the order of the products in clover_leaves.
+LEAF_PATHS = (
+    ((0, 0, 0, False), (1, 1, 0, False), (0, 0, 1, True), (1, 0, 0, True)),
+    ((1, 0, 0, False), (0, -1, 1, True), (1, -1, 0, True), (0, -1, 0, False)),
+    ((0, -1, 0, True), (1, -1, -1, True), (0, -1, -1, False), (1, 0, -1, False)),
+    ((1, 0, -1, True), (0, 0, -1, False), (1, 1, -1, False), (0, 0, 0, True)),
+)
+
+
+def _shift2(f, mu, om, nu, on):
+    """f(x + om mu + on nu)."""
+    return _shift(_shift(f, mu, om), nu, on)
+
+
+def clover_force_gamma(x_field, y_field):
+    """Gam_mn(x) for m < n: {(m, n): [Lt, Lz, Ly, Lx, 3, 3]} (Hermitian, traceless)."""
+    out = {}
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            lam = np.einsum("st,...tb,...sa->...ba", SIGMA[mu, nu], x_field, y_field.conj())
+            lam = lam - (np.trace(lam, axis1=-2, axis2=-1) / 3.0)[..., None, None] * np.eye(3)
+            out[(mu, nu)] = lam + _dag(lam)
+    return out
+
+
+def clover_force_coeffs(u, x_field, y_field, kappa, csw):
+    """Clover part of dS/deps^a for S = phi^dag (D_sw^dag D_sw)^-1 phi: [4, Lt, Lz, Ly, Lx, 8].
+
+    X = (D_sw^dag D_sw)^-1 phi and Y = D_sw X; the hopping part is
+    force.force_coeffs.  Links without the fermion boundary phase.
+    """
+    out = np.zeros((4,) + x_field.shape[:4] + (8,), dtype=np.float64)
+    gam = clover_force_gamma(x_field, y_field)
+    for (mu, nu), g in gam.items():
+        for path in LEAF_PATHS:
+            mats = []
+            for d, om, on, adj in path:
+                m = _shift2(u[mu if d == 0 else nu], mu, om, nu, on)
+                mats.append(_dag(m) if adj else m)
+            for k, (d, om, on, adj) in enumerate(path):
+                after = _mm(*mats[k + 1:]) if k < 3 else None
+                before = _mm(*mats[:k]) if k > 0 else None
+                chain = [m for m in (after, g, before) if m is not None]
+                if adj:
+                    w = _mm(*chain, mats[k])
+                    sign = -1.0
+                else:
+                    w = _mm(mats[k], *chain)
+                    sign = 1.0
+                tr = np.einsum("kab,...ba->...k", T_GEN, w).real
+                # the factor is the link at x + om mu + on nu: move the term there
+                out[mu if d == 0 else nu] += sign * 0.25 * kappa * csw * _shift2(tr, mu, -om, nu, -on)
+    return out
+
+
+def solve_normal_full_clover(u, b, kappa, bc, csw, tol=1e-10, x0=None, max_iter=100000):
+    """D_sw^dag D_sw x = b on the whole lattice by CG (A(x) built once, then
+    D_sw v = A v - kappa H v and D_sw^dag t = A t - kappa H^dag t)."""
+    a = clover_matrix(u, kappa, csw)
+
+    def op(v):
+        t = apply_site_matrix(a, v) - kappa * hop(u, v, bc)
+        return apply_site_matrix(a, t) - kappa * hop(u, t, bc, dagger=True)
+
+    return cg(op, b, x0, tol, max_iter)

@@ -18,7 +18,8 @@ starting at x along mu).
 Momenta: real p^a_mu(x), P = sum_a p^a T^a, kinetic energy K = sum p^2 / 2
 (Gaussian p of unit variance sample exp(-K)).  Pseudofermion phi = D^dag eta
 with Gaussian eta, S_F = phi^dag (D^dag D)^-1 phi, equal to |eta|^2 at the
-links phi was drawn on.  H = K + S_G + S_F.  Equations of motion
+links phi was drawn on.  H = K + S_G + S_F.  With a clover term (csw != 0)
+D is D_sw of clover.py throughout and the force adds its clover part.  Equations of motion
 dU/dt = i P U, dp^a/dt = -dS/deps^a.  Integrators over n steps of size
 eps = tau / n:
   leapfrog:  p -= eps/2 F;  n x [U <- exp(i eps P) U;  p -= eps F] with the
@@ -33,6 +34,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import clover
 from .force import T_GEN, force_coeffs, link_variation
 from .solve import solve_normal_full
 from .wilson import dirac, dirac_dag
@@ -100,16 +102,26 @@ def kinetic(p):
     return float(0.5 * np.sum(p * p))
 
 
-def fermion_action(u, phi, kappa, bc, tol=1e-12):
-    x, _, _ = solve_normal_full(u, phi, kappa, bc, tol=tol)
+def _solve(u, phi, kappa, bc, tol, csw):
+    if csw == 0.0:
+        return solve_normal_full(u, phi, kappa, bc, tol=tol)[0]
+    return clover.solve_normal_full_clover(u, phi, kappa, bc, csw, tol=tol)[0]
+
+
+def fermion_action(u, phi, kappa, bc, tol=1e-12, csw=0.0):
+    x = _solve(u, phi, kappa, bc, tol, csw)
     return float(np.vdot(phi.reshape(-1), x.reshape(-1)).real)
 
 
-def total_force(u, phi, beta, kappa, bc, tol=1e-12):
+def total_force(u, phi, beta, kappa, bc, tol=1e-12, csw=0.0):
     f = gauge_force(u, beta)
     if phi is not None:
-        x, _, _ = solve_normal_full(u, phi, kappa, bc, tol=tol)
-        f = f + force_coeffs(u, x, dirac(u, x, kappa, bc), kappa, bc)
+        x = _solve(u, phi, kappa, bc, tol, csw)
+        if csw == 0.0:
+            f = f + force_coeffs(u, x, dirac(u, x, kappa, bc), kappa, bc)
+        else:
+            y = clover.dirac_clover(u, x, kappa, bc, csw)
+            f = f + force_coeffs(u, x, y, kappa, bc) + clover.clover_force_coeffs(u, x, y, kappa, csw)
     return f
 
 
@@ -118,10 +130,10 @@ def update_links(u, p, eps):
     return link_variation(u, p, eps)
 
 
-def integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator="leapfrog", tol=1e-12):
+def integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator="leapfrog", tol=1e-12, csw=0.0):
     """Molecular-dynamics trajectory of length tau; returns (U, p)."""
     eps = tau / nsteps
-    force = lambda uu: total_force(uu, phi, beta, kappa, bc, tol)  # noqa: E731
+    force = lambda uu: total_force(uu, phi, beta, kappa, bc, tol, csw)  # noqa: E731
     u = np.array(u, copy=True)
     p = np.array(p, copy=True)
     if integrator == "leapfrog":
@@ -142,23 +154,28 @@ def integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator="leapfrog", to
     return u, p
 
 
-def hamiltonian(u, p, phi, beta, kappa, bc, tol=1e-12):
+def hamiltonian(u, p, phi, beta, kappa, bc, tol=1e-12, csw=0.0):
     h = kinetic(p) + gauge_action(u, beta)
     if phi is not None:
-        h += fermion_action(u, phi, kappa, bc, tol)
+        h += fermion_action(u, phi, kappa, bc, tol, csw)
     return h
 
 
-def trajectory(u, p, eta, beta, kappa, bc, tau, nsteps, integrator="leapfrog", uniform=0.5, tol=1e-12):
+def trajectory(u, p, eta, beta, kappa, bc, tau, nsteps, integrator="leapfrog", uniform=0.5, tol=1e-12, csw=0.0):
     """One HMC update: phi = D^dag eta, integrate, Metropolis.
 
     eta is None for the pure gauge theory.  Returns (U after the accept or
     reject, dH, accepted).
     """
-    phi = None if eta is None else dirac_dag(u, eta, kappa, bc)
+    if eta is None:
+        phi = None
+    elif csw == 0.0:
+        phi = dirac_dag(u, eta, kappa, bc)
+    else:
+        phi = clover.dirac_clover_dag(u, eta, kappa, bc, csw)
     h0 = kinetic(p) + gauge_action(u, beta) + (0.0 if eta is None else float(np.sum(np.abs(eta) ** 2)))
-    u1, p1 = integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator, tol)
-    dh = hamiltonian(u1, p1, phi, beta, kappa, bc, tol) - h0
+    u1, p1 = integrate(u, p, phi, beta, kappa, bc, tau, nsteps, integrator, tol, csw)
+    dh = hamiltonian(u1, p1, phi, beta, kappa, bc, tol, csw) - h0
     accept = bool(uniform <= np.exp(-dh))
     return (u1 if accept else np.array(u, copy=True)), dh, accept
 

@@ -290,3 +290,77 @@ def test_clover_sites_matches_whole_lattice():
     sites = np.arange(0, full.shape[0], 5)
     got = clv.clover_sites(u, kappa, csw, sites)
     assert np.max(np.abs(got - full[sites])) < 1e-14
+
+
+def test_clover_force_matches_bilinear_finite_difference():
+    """dS = -2 Re Y^dag dD_sw X: the hopping plus clover forces are the derivative of
+    -2 Re <Y, D_sw(U) X> at fixed X, Y, along a random direction on every link and
+    generator by generator on single links (a link hit twice by the 2-extents is
+    counted through both of its appearances)."""
+    dims = (4, 2, 2, 4)
+    kappa, csw = 0.12, 1.3
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(98, 0))
+    x = synth.gaussian_spinor(dims, synth.seed_for(98, 1))
+    y = synth.gaussian_spinor(dims, synth.seed_for(98, 2))
+    f = oracle.force_coeffs(u, x, y, kappa, BC_AP) + clv.clover_force_coeffs(u, x, y, kappa, csw)
+
+    def bilinear(omega, e):
+        ue = oracle.link_variation(u, omega, e)
+        return -2.0 * inner(y, clv.dirac_clover(ue, x, kappa, BC_AP, csw)).real
+
+    rng = np.random.default_rng(3)
+    omega = rng.standard_normal(f.shape)
+    h = 1e-4
+    fd = (bilinear(omega, h) - bilinear(omega, -h)) / (2 * h)
+    an = float(np.sum(omega * f))
+    assert abs(fd - an) < 1e-7 * abs(an)
+    for _ in range(6):
+        idx = (int(rng.integers(4)),) + tuple(int(rng.integers(n)) for n in f.shape[1:5]) + (int(rng.integers(8)),)
+        e = np.zeros_like(omega)
+        e[idx] = 1.0
+        fd = (bilinear(e, h) - bilinear(e, -h)) / (2 * h)
+        assert abs(fd - f[idx]) < 1e-7 * max(1.0, abs(f[idx])), (idx, fd, f[idx])
+
+
+def test_clover_force_is_the_derivative_of_the_action():
+    """S = phi^dag (D_sw^dag D_sw)^-1 phi, differentiated by central differences of
+    converged solves, against the force from X and Y = D_sw X."""
+    dims = (2, 2, 2, 4)
+    kappa, csw = 0.124, 1.0
+    u = synth.gauge_field(dims, 0.4, synth.seed_for(98, 3))
+    phi = synth.gaussian_spinor(dims, synth.seed_for(98, 4))
+
+    def action(uu):
+        xx, _, res = clv.solve_normal_full_clover(uu, phi, kappa, BC_AP, csw, tol=1e-14)
+        assert res < 1e-13
+        return inner(phi, xx).real
+
+    x, _, _ = clv.solve_normal_full_clover(u, phi, kappa, BC_AP, csw, tol=1e-14)
+    y = clv.dirac_clover(u, x, kappa, BC_AP, csw)
+    f = oracle.force_coeffs(u, x, y, kappa, BC_AP) + clv.clover_force_coeffs(u, x, y, kappa, csw)
+    omega = np.random.default_rng(4).standard_normal(f.shape)
+    h = 1e-4
+    fd = (action(oracle.link_variation(u, omega, h)) - action(oracle.link_variation(u, omega, -h))) / (2 * h)
+    an = float(np.sum(omega * f))
+    assert abs(fd - an) < 1e-6 * abs(an)
+
+
+def test_clover_force_vanishes_without_the_term_and_is_gauge_covariant():
+    dims = (4, 2, 2, 4)
+    kappa = 0.12
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(98, 5))
+    x = synth.gaussian_spinor(dims, synth.seed_for(98, 6))
+    y = synth.gaussian_spinor(dims, synth.seed_for(98, 7))
+    assert np.all(clv.clover_force_coeffs(u, x, y, kappa, 0.0) == 0.0)
+    f = clv.clover_force_coeffs(u, x, y, kappa, 1.5)
+    # gauge transformation: U_mu(x) -> W(x) U_mu(x) W(x + mu)^dag, psi(x) -> W(x) psi(x);
+    # the force matrix sum_a F^a T^a at each link rotates to W(x) F W(x)^dag
+    w = synth.gauge_field(dims, 2.0, synth.seed_for(98, 8))[0]
+    ug = np.stack([np.einsum("...ab,...bc,...dc->...ad", w, u[m], np.conj(clv._shift(w, m, 1))) for m in range(4)])
+    xg = np.einsum("...ab,...sb->...sa", w, x)
+    yg = np.einsum("...ab,...sb->...sa", w, y)
+    fg = clv.clover_force_coeffs(ug, xg, yg, kappa, 1.5)
+    tg = oracle.force.T_GEN
+    m = np.einsum("...k,kab->...ab", f, tg)
+    mg = np.einsum("...k,kab->...ab", fg, tg)
+    assert np.max(np.abs(mg - np.einsum("...ab,m...bc,...dc->m...ad", w, m, np.conj(w)))) < 1e-12 * np.max(np.abs(m))

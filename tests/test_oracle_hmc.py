@@ -9,12 +9,15 @@
   Omelyan, with and without fermions);
 - energy conservation: dH falls by about 4 when the step halves (both
   integrators are second order), and Omelyan's dH is below leapfrog's;
-- the start of a trajectory: S_F = |eta|^2 at phi = D^dag eta.
+- the start of a trajectory: S_F = |eta|^2 at phi = D^dag eta;
+- the same reversibility, second order and start with the clover term (a
+  missing or wrong clover force leaves dH first order in the step).
 """
 import numpy as np
 import pytest
 
 import oracle
+import oracle.clover as clover
 import oracle.hmc as hmc
 import synth
 from test_oracle_clover import _abelian_field
@@ -127,3 +130,22 @@ def test_gauge_force_links_matches_whole_lattice():
     got = hmc.gauge_force_links(u, 5.7, links)
     want = np.array([full[mu, i] for mu, i in links])
     assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_clover_trajectory_reversible_and_second_order():
+    """HMC with the clover term: the integrator is reversible, dH shrinks four-fold
+    when the step halves (the forces are the derivatives of H), and phi = D_sw^dag eta
+    gives S_F = |eta|^2 at the start."""
+    dims = (2, 2, 2, 4)
+    kappa, beta, csw = 0.12, 5.6, 1.2
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(97, 20))
+    p = momenta(dims, 21)
+    eta = synth.gaussian_spinor(dims, synth.seed_for(97, 22))
+    phi = clover.dirac_clover_dag(u, eta, kappa, BC_AP, csw)
+    e2 = np.sum(np.abs(eta) ** 2)
+    assert abs(hmc.fermion_action(u, phi, kappa, BC_AP, csw=csw) - e2) < 1e-10 * e2
+    u1, p1 = hmc.integrate(u, p, phi, beta, kappa, BC_AP, 0.4, 3, "omelyan", tol=1e-13, csw=csw)
+    u0, p0 = hmc.integrate(u1, -p1, phi, beta, kappa, BC_AP, 0.4, 3, "omelyan", tol=1e-13, csw=csw)
+    assert np.max(np.abs(u0 - u)) < 1e-10 and np.max(np.abs(-p0 - p)) < 1e-9
+    dh = {n: hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.5, n, "leapfrog", tol=1e-13, csw=csw)[1] for n in (4, 8)}
+    assert 3.0 < dh[4] / dh[8] < 5.0, dh
