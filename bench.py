@@ -570,6 +570,9 @@ def clover_measurements(cola, dev, u, b):
 # each, the product U V, and the staple sums (3x3 complex product = 27 complex
 # multiply-adds = 216 flop)
 GAUGE_FORCE_FLOP_PER_LINK = 13 * 216 + 5 * 18
+# clover force per link: for each of the three planes through it, 9 products
+# of 3x3 complex matrices per plaquette (two plaquettes), then U S+ and S- U^dag
+CLOVER_FORCE_FLOP_PER_LINK = (3 * 2 * 9 + 2) * 216
 
 
 def hmc_measurements(cola, dev):
@@ -582,7 +585,8 @@ def hmc_measurements(cola, dev):
     D^dag D or as two even-odd Dirac-system solves (the same X), each with
     FP32 or FP16 inner iterations, after one warm-up trajectory of each; the
     fastest is reported in front.  Also the isolated gauge-force and
-    link-update kernels.
+    link-update kernels, the fermion force with and without the clover term,
+    and the trajectory with the clover term (c_sw = 1).
     """
     import torch
 
@@ -627,6 +631,16 @@ def hmc_measurements(cola, dev):
     zero = torch.zeros_like(mom)
     lu_us = kernel_us(lambda: cola.link_update(g, u, zero, 0.0))
     gf_tflops = GAUGE_FORCE_FLOP_PER_LINK * 4 * vol / (gf_us * 1e-6) / 1e12
+    # the fermion force without and with the clover term (c_sw = 1), and the
+    # trajectory with the clover term in the fastest solve configuration
+    ff_us = kernel_us(lambda: cola.fermion_force(g, eta, eta))
+    g.attach_clover(1.0)
+    ffc_us = kernel_us(lambda: cola.fermion_force(g, eta, eta))
+    trajectory(*best)  # warm-up of the clover kernels' launch shapes
+    info_c = trajectory(*best)
+    g.attach_clover(0.0)
+    cf_us = ffc_us - ff_us
+    cf_tflops = CLOVER_FORCE_FLOP_PER_LINK * 4 * vol / (cf_us * 1e-6) / 1e12
     return {
         "lattice": "24x24x24x48", "beta": 5.6, "kappa": 0.124, "tau": 0.5, "steps": 5, "integrator": "omelyan",
         "md_solves": f"{best[0]} ({'CG on D^dag D' if best[0] == 'full' else 'D W = g5 phi, D X = g5 W'}), "
@@ -636,6 +650,10 @@ def hmc_measurements(cola, dev):
         "variants_s": {f"{k[0]}/{k[1]}": v.seconds for k, v in variants.items()},
         "gauge_force_us": gf_us, "gauge_force_fp64_tflops": gf_tflops, "gauge_force_frac_fp64": gf_tflops / FP64_PEAK_TFLOPS,
         "link_update_and_repack_us": lu_us,
+        "fermion_force_us": ff_us, "clover_force_us": cf_us, "clover_force_fp64_tflops": cf_tflops,
+        "clover_force_frac_fp64": cf_tflops / FP64_PEAK_TFLOPS,
+        "clover_trajectory": {"csw": 1.0, "trajectory_s": info_c.seconds, "cg_iters": info_c.cg_iters,
+                              "dH": info_c.dH, "accepted": info_c.accepted},
     }
 
 

@@ -166,8 +166,9 @@ cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const void *in, in
  * the handle holds (72 reals per site each; FP16 without a scale).  From then
  * on cola_dirac_apply, cola_mdagm_apply(_noalloc) and cola_cg_solve(_batched)
  * use the clover operator, cola_gauge_update rebuilds the term for the new
- * links, and cola_fermion_force / cola_dirac_link_grad return
- * COLA_ERR_UNSUPPORTED (they differentiate the hopping term only).
+ * links, cola_fermion_force adds the clover term's force and
+ * cola_hmc_trajectory integrates the clover action; cola_dirac_link_grad
+ * returns COLA_ERR_UNSUPPORTED (it differentiates the hopping term only).
  * cola_dslash_apply stays the bare hopping term.  csw = 0 removes the term.
  * The call waits for its stream (it reads back a pivot flag): it returns
  * COLA_ERR_BREAKDOWN, and leaves the handle without a clover term, if some
@@ -281,7 +282,14 @@ cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *evals, const 
  * F^a_mu(x) = dS/d eps^a for U_mu(x) -> (1 + i eps T^a) U_mu(x), T^a = lambda^a/2:
  * F^a = -2 kappa Im Tr[T^a Ut_mu(x) (P + Q^dag)], with
  * P_ba = sum_s [(1-gamma_mu) X(x+mu)]_sb conj(Y(x)_sa),
- * Q_ba = sum_s [(1+gamma_mu) X(x)]_sb conj(Y(x+mu)_sa).  Accumulated in FP64. */
+ * Q_ba = sum_s [(1+gamma_mu) X(x)]_sb conj(Y(x+mu)_sa).  Accumulated in FP64.
+ * With a clover term (D = A - kappa H, Y = D X) the clover part is added:
+ * dS = -2 Re Y^dag dA X = (kappa c_sw / 4) sum_x sum_{mu<nu} Im Tr[dQ_munu Gam_munu],
+ * Gam_munu(x) = L + L^dag, L the traceless part of
+ * Lam_ba = sum_st (sigma_munu)_st X(x)_tb conj(Y(x)_sa); each link collects the
+ * two plaquettes of each of its three planes with Gam inserted at their four
+ * corners (the links without boundary phases).  That part needs 384 bytes
+ * of handle workspace per site. */
 cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_dev,
                                const void *Y_dev, cudaStream_t stream);
 
@@ -344,8 +352,9 @@ typedef struct {
 } cola_hmc_info;
 
 /* One HMC update of the gauge field links_dev (canonical FP64, device, in
- * and out; the handle must be created from or last updated with it, hold
- * FP64 links and have no clover term) with momenta mom_dev (FP64 [4][V][8],
+ * and out; the handle must be created from or last updated with it and hold
+ * FP64 links; with a clover term D = A - kappa H throughout, the term rebuilt
+ * after every link update) with momenta mom_dev (FP64 [4][V][8],
  * device, drawn by the caller from N(0, 1); on return the final momenta of
  * the trajectory) and pseudofermion source eta_dev (canonical spinor,
  * device, drawn by the caller; NULL for the pure gauge theory).

@@ -19,8 +19,9 @@ definitions, each stated where it is coded:
              even-odd normal-equation solve, shifted systems (A + sigma_i) x_i = b
              one CG per shift, dense matrices for brute force
   force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
-  clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H
-             and its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe
+  clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H,
+             its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe and
+             the clover term's part of the fermion force
   hmc.py     Wilson gauge action and force, momenta, leapfrog and Omelyan
              integrators, the Hamiltonian and the Metropolis step
   eig.py     the lowest eigenpairs of D^dag D and Mhat^dag Mhat (dense and
@@ -35,9 +36,10 @@ an exactly computed action and against the closed form S = |eta|^2 at
 phi = D^dag eta; for the clover term the unit-gauge reduction, a constant
 abelian field in closed form, the weak-field lattice curl, gauge covariance,
 dense Schur identities and the tree-level cancellation of the Wilson lift of
-Landau zero modes (which fixes its sign); for HMC the gauge force against
+Landau zero modes (which fixes its sign), and its force against finite
+differences of the bilinear -2 Re Y^dag D_sw X and of the action; for HMC the gauge force against
 finite differences of the action, exact free motion, reversibility and the
-second-order scaling of dH; for the eigenmodes the closed-form free-field
+second-order scaling of dH (with and without the clover term); for the eigenmodes the closed-form free-field
 spectra of D^dag D and Mhat^dag Mhat (derived in eig.py).  Every function
 here is pinned by at least one of them.
 """

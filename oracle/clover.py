@@ -253,3 +253,64 @@ def solve_normal_full_clover(u, b, kappa, bc, csw, tol=1e-10, x0=None, max_iter=
         return apply_site_matrix(a, t) - kappa * hop(u, t, bc, dagger=True)
 
     return cg(op, b, x0, tol, max_iter)
+
+
+def clover_force_links(u, x_field, y_field, kappa, csw, links):
+    """clover_force_coeffs at a list of (mu, lexicographic site) links: [n, 8].
+
+    Per-link restatement with explicit coordinate arithmetic, for sampled
+    checks on lattices too large for the whole-lattice form: every factor of
+    every leaf of every plane through the link that stands for it.
+    """
+    _, lt, lz, ly, lx = u.shape[:5]
+    dims = (lx, ly, lz, lt)
+
+    def coords(i):
+        return [i % lx, (i // lx) % ly, (i // (lx * ly)) % lz, i // (lx * ly * lz)]
+
+    def at(field, c):
+        return field[c[3], c[2], c[1], c[0]]
+
+    def moved(c, steps):
+        return [(c[k] + steps[k]) % dims[k] for k in range(4)]
+
+    out = np.zeros((len(links), 8))
+    for n, (rho, i) in enumerate(links):
+        y = coords(int(i))
+        for mu in range(4):
+            for nu in range(mu + 1, 4):
+                if rho not in (mu, nu):
+                    continue
+                for path in LEAF_PATHS:
+                    for k, (d, om, on, adj) in enumerate(path):
+                        if (mu if d == 0 else nu) != rho:
+                            continue
+                        step = [0, 0, 0, 0]
+                        step[mu] -= om
+                        step[nu] -= on
+                        xs = moved(y, step)  # the leaf's base site: the factor sits at x + om mu + on nu = y
+                        mats = []
+                        for dd, omm, onn, aa in path:
+                            s2 = [0, 0, 0, 0]
+                            s2[mu] += omm
+                            s2[nu] += onn
+                            m = at(u[mu if dd == 0 else nu], moved(xs, s2))
+                            mats.append(m.conj().T if aa else m)
+                        xv, yv = at(x_field, xs), at(y_field, xs)
+                        lam = np.einsum("st,tb,sa->ba", SIGMA[mu, nu], xv, yv.conj())
+                        lam = lam - np.trace(lam) / 3.0 * np.eye(3)
+                        g = lam + lam.conj().T
+                        after = np.eye(3, dtype=np.complex128)
+                        for m in mats[k + 1:]:
+                            after = after @ m
+                        before = np.eye(3, dtype=np.complex128)
+                        for m in mats[:k]:
+                            before = before @ m
+                        if adj:
+                            w = after @ g @ before @ mats[k]
+                            sign = -1.0
+                        else:
+                            w = mats[k] @ after @ g @ before
+                            sign = 1.0
+                        out[n] += sign * 0.25 * kappa * csw * np.einsum("kab,ba->k", T_GEN, w).real
+    return out

@@ -301,7 +301,9 @@ def eig_lowest(g: Gauge, v0: torch.Tensor, nev: int | None = None, op="eo", tol=
 
 
 def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
-    """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X."""
+    """F^a_mu(x) = dS/deps^a for S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X.
+
+    With a clover term attached, D = A - kappa H and the clover term's force is included."""
     lx, ly, lz, lt = g.dims
     out = torch.empty((4, lt, lz, ly, lx, 8), dtype=torch.float64, device=g.device)
     check(g.lib.cola_fermion_force(g.handle, _ptr(out), _complex_field(X, g.volume * 12, "X"),

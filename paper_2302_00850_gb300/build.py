@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcola.so")
-SOURCES = ["dslash.cu", "dslash_clover.cu", "clover.cu", "blas.cu", "pack.cu", "force.cu", "gauge.cu", "hmc.cu",
+SOURCES = ["dslash.cu", "dslash_clover.cu", "clover.cu", "clover_force.cu", "blas.cu", "pack.cu", "force.cu", "gauge.cu", "hmc.cu",
            "solver.cu", "multishift.cu", "eig.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -248,7 +248,7 @@ static cola_status check_rhs(int nrhs) {
 }
 
 static cola_status clover_unsupported(const char *what) {
-    set_error(std::string(what) + " differentiates the Wilson hopping term only; the handle has a clover term");
+    set_error(std::string(what) + " differentiates the hopping term only; the handle has a clover term");
     return COLA_ERR_UNSUPPORTED;
 }
 
@@ -424,10 +424,15 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
     TraceRange trace_("cola_fermion_force");
     if (!g || !force_dev || !X_dev || !Y_dev) return arg_error("null argument to cola_fermion_force");
     COLA_TRY(check_prec(g, COLA_F64));
-    if (g->csw != 0.0) return clover_unsupported("cola_fermion_force");
-    return cuda_check(launch_force(g->geom, g->lat.kappa, g->links[COLA_F64], g->recon[COLA_F64], force_dev, X_dev,
-                                   Y_dev, stream),
-                      "force launch");
+    COLA_CUDA(launch_force(g->geom, g->lat.kappa, g->links[COLA_F64], g->recon[COLA_F64], force_dev, X_dev, Y_dev,
+                           stream),
+              "force launch");
+    if (g->csw == 0.0) return COLA_OK;
+    void *scratch;
+    COLA_TRY(ws_slot(g, cola_gauge_s::kSlotCloverForce, clover_force_scratch_bytes(g->geom), &scratch));
+    return cuda_check(launch_clover_force(g->geom, g->links[COLA_F64], g->recon[COLA_F64], g->lat.kappa, g->csw,
+                                          X_dev, Y_dev, force_dev, 1.0, true, scratch, stream),
+                      "clover force launch");
 }
 
 cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev, const void *gy_dev,

@@ -295,6 +295,11 @@ static CloverSigma make_sigma() {
     return sg;
 }
 
+const CloverSigma &clover_sigma() {
+    static const CloverSigma sig = make_sigma();
+    return sig;
+}
+
 void set_clover(DslashLat &L, cola_gauge g, int prec, bool inverse) {
     L.clv = inverse ? g->clover_inv[prec] : g->clover[prec];
     L.clv_parity_stride = clover_parity_bytes(prec, g->geom.Vh);
@@ -322,7 +327,7 @@ cola_status clover_rebuild(cola_gauge g, cudaStream_t s) {
     if (st != COLA_OK) return st;
     st = cuda_check(cudaMemsetAsync(bad, 0, sizeof(int), s), "clover flag");
     if (st != COLA_OK) return st;
-    static const CloverSigma sig = make_sigma();
+    const CloverSigma &sig = clover_sigma();
     st = cuda_check(launch_clover_build(g->geom, g->links[COLA_F64], g->recon[COLA_F64], g->lat.kappa * g->csw, sig,
                                         g->clover, g->clover_inv, bad, s),
                     "clover construction");

@@ -1,0 +1,266 @@
+// Clover part of the HMC fermion force.
+//
+// The paper's overview of COLA's physics features lists clover-improved
+// fermions and HMC; it writes neither the action nor its force.  With the
+// clover term A = 1 - kappa c_sw sum_{mu<nu} sigma_munu F_munu of clover.cu and
+// S = phi^dag (D^dag D)^-1 phi, X = (D^dag D)^-1 phi, Y = D X, the variation
+// dS = -2 Re Y^dag dA X of the clover term is
+//   dS = (kappa c_sw / 4) sum_x sum_{mu<nu} Im Tr[dQ_munu(x) Gam_munu(x)],
+//   Gam_munu = L + L^dag, L = Lam - tr Lam / 3,
+//   Lam_munu(x)_ba = sum_st (sigma_munu)_st X(x)_tb conj(Y(x)_sa)
+// (the traceless projection of F moves onto Lam, and the anti-Hermitian part
+// of Q pairs with the Hermitian part of Lam).  Ordered pairs (mu, nu) and
+// (nu, mu) give the same sum (Q_numu = Q_munu^dag, Gam_numu = -Gam_munu), so
+// the link U_mu(y) collects, for each nu != mu, the two plaquettes of the
+// (mu, nu) plane through it with Gam inserted at each of their four corners:
+//   Z = U S+ - S- U^dag,
+//   S+ = L2 L3 L4 G(y) + G(y+mu) L2 L3 L4 + L2 G(y+mu+nu) L3 L4 + L2 L3 G(y+nu) L4,
+//        L2 = U_nu(y+mu), L3 = U_mu(y+nu)^dag, L4 = U_nu(y)^dag,
+//   S- = G(y) M1 M2 M3 + M1 G(y-nu) M2 M3 + M1 M2 G(y-nu+mu) M3 + M1 M2 M3 G(y+mu),
+//        M1 = U_nu(y-nu)^dag, M2 = U_mu(y-nu), M3 = U_nu(y-nu+mu),
+// with G = Gam_munu (= -Gam_numu for mu > nu), and
+//   dS/deps^a = (kappa c_sw / 4) Re Tr[T^a Z]   (U -> (1 + i eps T^a) U).
+// Two kernels, FP64 throughout: Gam on every site (six planes, eight reals
+// each: Gam is Hermitian and traceless), then one thread per link.
+#include "cola_impl.h"
+
+namespace cola {
+namespace {
+
+using C64 = Cx<double>;
+
+// Gam layout: [plane][8][V] doubles, plane = (0,1) (0,2) (0,3) (1,2) (1,3) (2,3),
+// reals g00, g11 (g22 = -g00 - g11), then (0,1) (0,2) (1,2) as (re, im).
+constexpr int kGamReals = 8;
+
+__device__ __forceinline__ int plane_of(int mu, int nu) {  // mu < nu
+    return mu == 0 ? nu - 1 : mu == 1 ? nu + 1 : 5;
+}
+
+__global__ void __launch_bounds__(128) clover_gamma_kernel(const Geom g, const CloverSigma sig, const double2 *X,
+                                                           const double2 *Y, double *gam) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    C64 x[12], y[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const double2 a = __ldg(X + (size_t)i * 12 + c), b = __ldg(Y + (size_t)i * 12 + c);
+        x[c] = {a.x, a.y};
+        y[c] = {b.x, b.y};
+    }
+    for (int p = 0; p < 6; ++p) {
+        C64 lam[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) lam[k] = {0.0, 0.0};
+        // Lam_ba = sum over the chirality blocks of sigma_st X_tb conj(Y_sa)
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const C64 sg = {sig.v[p][chi][2 * s + t][0], sig.v[p][chi][2 * s + t][1]};
+                    if (sg.re == 0.0 && sg.im == 0.0) continue;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const C64 sx = cmul(sg, x[(2 * chi + t) * 3 + b]);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const C64 v = cmulc(sx, y[(2 * chi + s) * 3 + a]);
+                            lam[3 * b + a].re += v.re;
+                            lam[3 * b + a].im += v.im;
+                        }
+                    }
+                }
+        // Gam = L + L^dag, L = Lam - tr Lam / 3: the trace only moves the diagonal
+        const double tr = (lam[0].re + lam[4].re + lam[8].re) / 3.0;
+        double *o = gam + (size_t)p * kGamReals * g.V + i;
+        o[0 * (size_t)g.V] = 2.0 * (lam[0].re - tr);
+        o[1 * (size_t)g.V] = 2.0 * (lam[4].re - tr);
+        o[2 * (size_t)g.V] = lam[1].re + lam[3].re;  // (0,1)
+        o[3 * (size_t)g.V] = lam[1].im - lam[3].im;
+        o[4 * (size_t)g.V] = lam[2].re + lam[6].re;  // (0,2)
+        o[5 * (size_t)g.V] = lam[2].im - lam[6].im;
+        o[6 * (size_t)g.V] = lam[5].re + lam[7].re;  // (1,2)
+        o[7 * (size_t)g.V] = lam[5].im - lam[7].im;
+    }
+}
+
+__device__ __forceinline__ int lex_site(const Geom &g, const int (&p)[4]) {
+    const int x = wrap_coord(p[0], g.L[0]), y = wrap_coord(p[1], g.L[1]);
+    const int z = wrap_coord(p[2], g.L[2]), t = wrap_coord(p[3], g.L[3]);
+    return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+}
+
+// G = sign Gam_plane at the site with coordinates p (wrapped)
+__device__ __forceinline__ void gam_at(const Geom &g, const double *gam, int plane, double sign, const int (&p)[4],
+                                       C64 (&m)[9]) {
+    const double *q = gam + (size_t)plane * kGamReals * g.V + lex_site(g, p);
+    const size_t V = g.V;
+    const double d0 = sign * __ldg(q), d1 = sign * __ldg(q + V);
+    const C64 e01 = {sign * __ldg(q + 2 * V), sign * __ldg(q + 3 * V)};
+    const C64 e02 = {sign * __ldg(q + 4 * V), sign * __ldg(q + 5 * V)};
+    const C64 e12 = {sign * __ldg(q + 6 * V), sign * __ldg(q + 7 * V)};
+    m[0] = {d0, 0.0};
+    m[4] = {d1, 0.0};
+    m[8] = {-d0 - d1, 0.0};
+    m[1] = e01;
+    m[2] = e02;
+    m[5] = e12;
+    m[3] = {e01.re, -e01.im};
+    m[6] = {e02.re, -e02.im};
+    m[7] = {e12.re, -e12.im};
+}
+
+// c = a b
+__device__ __forceinline__ void mul3(const C64 (&a)[9], const C64 (&b)[9], C64 (&c)[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            C64 s = cmul(a[3 * i], b[j]);
+            cmac(s, a[3 * i + 1], b[3 + j]);
+            cmac(s, a[3 * i + 2], b[6 + j]);
+            c[3 * i + j] = s;
+        }
+}
+
+// acc += a b
+__device__ __forceinline__ void mac3(C64 (&acc)[9], const C64 (&a)[9], const C64 (&b)[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cmac(acc[3 * i + j], a[3 * i], b[j]);
+            cmac(acc[3 * i + j], a[3 * i + 1], b[3 + j]);
+            cmac(acc[3 * i + j], a[3 * i + 2], b[6 + j]);
+        }
+}
+
+__device__ __forceinline__ void adj3(C64 (&m)[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        m[4 * i].im = -m[4 * i].im;
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) {
+            const C64 a = m[3 * i + j], b = m[3 * j + i];
+            m[3 * i + j] = {b.re, -b.im};
+            m[3 * j + i] = {a.re, -a.im};
+        }
+    }
+}
+
+// op(U_dir(y + dmu mu + dnu nu)), op = identity or adjoint
+template <int RECON>
+__device__ __forceinline__ void link_off(const Geom &g, const char *links, size_t dir_stride, const int (&c)[4],
+                                         int dir, int mu, int dmu, int nu, int dnu, bool adj, C64 (&u)[9]) {
+    int p[4] = {c[0], c[1], c[2], c[3]};
+    p[mu] += dmu;
+    p[nu] += dnu;
+    link_at<RECON>(g, links, dir_stride, p, dir, u);
+    if (adj) adj3(u);
+}
+
+// sign Gam_plane(y + dmu mu + dnu nu)
+__device__ __forceinline__ void gam_off(const Geom &g, const double *gam, int plane, double sign, const int (&c)[4],
+                                        int mu, int dmu, int nu, int dnu, C64 (&m)[9]) {
+    int p[4] = {c[0], c[1], c[2], c[3]};
+    p[mu] += dmu;
+    p[nu] += dnu;
+    gam_at(g, gam, plane, sign, p, m);
+}
+
+template <int RECON>
+__global__ void __launch_bounds__(128) clover_force_kernel(const Geom g, const char *links, size_t dir_stride,
+                                                           const double *gam, double *out, double coef,
+                                                           int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mu = blockIdx.y;
+    if (i >= g.V) return;
+    int c[4];
+    c[0] = i % g.L[0];
+    int r = i / g.L[0];
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+
+    C64 sp[9], sm[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sp[k] = sm[k] = {0.0, 0.0};
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        const int plane = mu < nu ? plane_of(mu, nu) : plane_of(nu, mu);
+        const double sign = mu < nu ? 1.0 : -1.0;
+        C64 a[9], b[9], d[9], gm[9], t[9];
+        // ---- the plaquette on the +nu side: L2 = U_nu(y+mu), L3 = U_mu(y+nu)^dag, L4 = U_nu(y)^dag
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, 0, false, a);  // L2
+        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, 1, true, b);   // L3
+        mul3(a, b, d);                                                         // L2 L3
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 1, gm);                     // G(y+mu+nu)
+        mul3(a, gm, t);                                                        // L2 G
+        mul3(t, b, a);                                                         // L2 G L3 (a free)
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, 0, true, b);   // L4 (L3 free)
+        mac3(sp, a, b);                                                        // + L2 G(y+mu+nu) L3 L4
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 1, gm);                     // G(y+nu)
+        mul3(d, gm, t);
+        mac3(sp, t, b);                                                        // + L2 L3 G(y+nu) L4
+        mul3(d, b, a);                                                         // L2 L3 L4
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                     // G(y)
+        mac3(sp, a, gm);                                                       // + L2 L3 L4 G(y)
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                     // G(y+mu)
+        mac3(sp, gm, a);                                                       // + G(y+mu) L2 L3 L4
+        // ---- the plaquette on the -nu side: M1 = U_nu(y-nu)^dag, M2 = U_mu(y-nu), M3 = U_nu(y-nu+mu)
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, -1, true, a);  // M1
+        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, -1, false, b); // M2
+        mul3(a, b, d);                                                         // M1 M2
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, -1, gm);                    // G(y-nu)
+        mul3(a, gm, t);                                                        // M1 G
+        mul3(t, b, a);                                                         // M1 G M2 (a free)
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, -1, false, b); // M3 (M2 free)
+        mac3(sm, a, b);                                                        // + M1 G(y-nu) M2 M3
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, -1, gm);                    // G(y-nu+mu)
+        mul3(d, gm, t);
+        mac3(sm, t, b);                                                        // + M1 M2 G(y-nu+mu) M3
+        mul3(d, b, a);                                                         // M1 M2 M3
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                     // G(y)
+        mac3(sm, gm, a);                                                       // + G(y) M1 M2 M3
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                     // G(y+mu)
+        mac3(sm, a, gm);                                                       // + M1 M2 M3 G(y+mu)
+    }
+    // Z = U S+ - S- U^dag; F^a = coef Re Tr[lambda^a Z] = coef Im Tr[lambda^a (i Z)]
+    C64 u[9], z[9], w[9];
+    link_at<RECON>(g, links, dir_stride, c, mu, u);
+    mul3(u, sp, z);
+    adj3(u);
+    mul3(sm, u, w);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = {-(z[k].im - w[k].im), z[k].re - w[k].re};  // i (z - w)
+    double fa[8];
+    im_tr_lambda(w, fa);
+    store_force(out + ((size_t)mu * g.V + i) * 8, fa, coef, accumulate != 0);
+}
+
+}  // namespace
+
+size_t clover_force_scratch_bytes(const Geom &g) { return (size_t)6 * kGamReals * g.V * sizeof(double); }
+
+cudaError_t launch_clover_force(const Geom &g, const void *links_f64, int recon, double kappa, double csw,
+                                const void *X, const void *Y, double *force, double coef, bool accumulate,
+                                void *scratch, cudaStream_t s) {
+    double *gam = static_cast<double *>(scratch);
+    const dim3 block(128), grid1((g.V + 127) / 128), grid2((g.V + 127) / 128, 4);
+    clover_gamma_kernel<<<grid1, block, 0, s>>>(g, clover_sigma(), static_cast<const double2 *>(X),
+                                                static_cast<const double2 *>(Y), gam);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const char *l = static_cast<const char *>(links_f64);
+    const size_t ds = link_dir_bytes(COLA_F64, recon, g.Vh);
+    // dS/deps^a = (kappa c_sw / 4) Re Tr[T^a Z] = (kappa c_sw / 8) Re Tr[lambda^a Z]
+    const double c = coef * kappa * csw / 8.0;
+    if (recon == 12) clover_force_kernel<12><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
+    else clover_force_kernel<18><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace cola

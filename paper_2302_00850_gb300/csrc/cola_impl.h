@@ -77,6 +77,17 @@ struct CloverSigma {
 // *bad is set to 1 if a block of A has a zero or non-finite pivot.
 cudaError_t launch_clover_build(const Geom &g, const void *links_f64, int recon, double coef, const CloverSigma &sig,
                                 void *const a[3], void *const ainv[3], int *bad, cudaStream_t s);
+// sigma_munu in the hopping kernel's basis, by plane and chirality block
+const CloverSigma &clover_sigma();
+// Bytes of scratch launch_clover_force needs (six Hermitian traceless 3x3
+// matrices per site).
+size_t clover_force_scratch_bytes(const Geom &g);
+// force = coef F_clover (accumulate: force += ...), [4][V][8]: the clover
+// term's part of dS/deps^a for S = phi^dag (D^dag D)^-1 phi from canonical
+// FP64 X = (D^dag D)^-1 phi and Y = D X, with the FP64 links of the handle.
+cudaError_t launch_clover_force(const Geom &g, const void *links_f64, int recon, double kappa, double csw,
+                                const void *X, const void *Y, double *force, double coef, bool accumulate,
+                                void *scratch, cudaStream_t s);
 // out_p = C_p in_p on the parities of parity_mask (1 even, 2 odd, 3 both).
 cudaError_t launch_clover_apply(int prec, const Geom &g, const void *clv, void *out, const void *in, int nrhs,
                                 int parity_mask, cudaStream_t s);
@@ -181,8 +192,9 @@ struct cola_gauge_s {
     int recon[3] = {12, 12, 12};
     size_t link_parity_bytes[3] = {0, 0, 0};
     // workspace slots: each a device buffer reused across calls
-    static constexpr int kSlots = 24;
+    static constexpr int kSlots = 25;
     static constexpr int kSlotCloverFlag = kSlots - 1;  // the construction's pivot flag
+    static constexpr int kSlotCloverForce = 23;         // the clover force's per-site matrices
     // HMC: saved links, phi, X, Y, two packed FP64 fields, reduction scratch
     static constexpr int kSlotHmc = 15;
     static constexpr int kSlotMultishift = 22;  // the multi-shift solver's workspace block

@@ -8,7 +8,9 @@
 // handle, and the Hamiltonian's terms are deterministic FP64 reductions read
 // back at the start and the end.  Each fermion force is a CG solve of
 // D^dag D X = phi from a zero guess (so that the trajectory is reversible up
-// to the solver tolerance), Y = D X, and the fermion-force kernel.
+// to the solver tolerance), Y = D X, and the fermion-force kernel (plus the
+// clover force when the handle has a clover term: D = A - kappa H throughout,
+// in phi = D^dag eta, the solves, Y and the force).
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -82,6 +84,7 @@ struct Traj {
     const cola_hmc_params *prm;
     cudaStream_t s;
     void *saved, *phi, *X, *Y, *pa, *pb;
+    void *clv_scratch = nullptr;
     double *scratch, *res;
     int force_evals = 0;
     int cg_iters = 0;
@@ -131,6 +134,10 @@ cola_status force(Traj &T, double coef) {
     HMC_TRY(dirac_canon(g, T.Y, T.X, false, T.pa, T.pb, T.s));
     HMC_CUDA(launch_force(G, g->lat.kappa, g->links[COLA_F64], g->recon[COLA_F64], T.mom, T.X, T.Y, T.s, coef, true),
              "fermion force");
+    if (g->csw != 0.0)
+        HMC_CUDA(launch_clover_force(G, g->links[COLA_F64], g->recon[COLA_F64], g->lat.kappa, g->csw, T.X, T.Y, T.mom,
+                                     coef, true, T.clv_scratch, T.s),
+                 "clover force");
     return COLA_OK;
 }
 
@@ -246,10 +253,6 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
     if (!g || !links_dev || !mom_dev || !params || !info) return arg_error("null argument to cola_hmc_trajectory");
     HMC_TRY(check_hmc_params(params));
     HMC_TRY(need_f64(g));
-    if (g->csw != 0.0) {
-        set_error("cola_hmc_trajectory integrates the Wilson action; the handle has a clover term");
-        return COLA_ERR_UNSUPPORTED;
-    }
     const auto t0 = std::chrono::steady_clock::now();
     const Geom &G = g->geom;
     Traj T;
@@ -271,6 +274,8 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
         HMC_TRY(ws_slot(g, k + 3, sp, &T.Y));
         HMC_TRY(ws_slot(g, k + 4, pk, &T.pa));
         HMC_TRY(ws_slot(g, k + 5, pk, &T.pb));
+        if (g->csw != 0.0)
+            HMC_TRY(ws_slot(g, cola_gauge_s::kSlotCloverForce, clover_force_scratch_bytes(G), &T.clv_scratch));
     }
     HMC_CUDA(cudaMemcpyAsync(T.saved, links_dev, link_canon_bytes(G), cudaMemcpyDeviceToDevice, stream), "save links");
     if (eta_dev) HMC_TRY(dirac_canon(g, T.phi, eta_dev, true, T.pa, T.pb, stream));

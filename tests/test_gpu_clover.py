@@ -240,8 +240,6 @@ def test_calls_that_refuse_a_clover_handle(cola):
     u, psi = lattice_inputs(dims, config=72)
     g = clover_gauge(cola, u, dims)
     with pytest.raises(cola.ColaError, match="clover"):
-        cola.fermion_force(g, to_dev(psi), to_dev(psi))
-    with pytest.raises(cola.ColaError, match="clover"):
         cola.dirac_link_grad(g, to_dev(psi), to_dev(psi))
     g32 = cola.Gauge(to_dev(u), dims, KAPPA, BC_AP, precisions=("f32",))
     with pytest.raises(cola.ColaError, match="FP64"):

@@ -162,9 +162,6 @@ def test_hmc_argument_errors(cola):
         cola.hmc_trajectory(g, ud, pd, None, BETA, 1.0, 0)
     with pytest.raises(cola.ColaError, match="uniform"):
         cola.hmc_trajectory(g, ud, pd, None, BETA, 1.0, 2, uniform=1.0)
-    g.attach_clover(1.0)
-    with pytest.raises(cola.ColaError, match="clover"):
-        cola.hmc_trajectory(g, ud, pd, None, BETA, 1.0, 2)
     g32 = cola.Gauge(ud, dims, KAPPA, BC_AP, precisions=("f32",))
     with pytest.raises(cola.ColaError, match="FP64"):
         cola.plaquette(g32)

@@ -12,7 +12,11 @@ Checked against what the definitions fix without re-typing them:
 - gauge covariance of A(x) and of D_sw;
 - gamma5 hermiticity of D_sw and Mhat;
 - the even-odd Schur complement and determinant identity on dense 2^4
-  matrices, and a CG solve of the even-odd normal system against dense LU.
+  matrices, and a CG solve of the even-odd normal system against dense LU;
+- the clover force: central finite differences of -2 Re <Y, D_sw(U) X> (all
+  links at once and single (link, generator) pairs) and of the action
+  phi^dag (D_sw^dag D_sw)^-1 phi, zero at c_sw = 0, gauge covariance, and the
+  per-link form against the whole-lattice form.
 """
 import numpy as np
 import pytest
@@ -364,3 +368,17 @@ def test_clover_force_vanishes_without_the_term_and_is_gauge_covariant():
     m = np.einsum("...k,kab->...ab", f, tg)
     mg = np.einsum("...k,kab->...ab", fg, tg)
     assert np.max(np.abs(mg - np.einsum("...ab,m...bc,...dc->m...ad", w, m, np.conj(w)))) < 1e-12 * np.max(np.abs(m))
+
+
+def test_clover_force_links_matches_whole_lattice():
+    dims = (4, 6, 2, 4)
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(98, 9))
+    x = synth.gaussian_spinor(dims, synth.seed_for(98, 10))
+    y = synth.gaussian_spinor(dims, synth.seed_for(98, 11))
+    f = clv.clover_force_coeffs(u, x, y, 0.13, 1.1).reshape(4, -1, 8)
+    rng = np.random.default_rng(12)
+    vol = int(np.prod(dims))
+    links = [(0, 0), (3, vol - 1)] + [(int(m), int(i)) for m, i in zip(rng.integers(0, 4, 40), rng.integers(0, vol, 40))]
+    got = clv.clover_force_links(u, x, y, 0.13, 1.1, links)
+    want = np.array([f[m, i] for m, i in links])
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
