@@ -769,7 +769,8 @@ def run_dslash_only(args):
 
 
 def run_gauge_only(args):
-    """Gauge force and link update kernels only on --lattice (the case profiled with ncu)."""
+    """Gauge force and link update kernels only on --lattice (the case profiled with ncu);
+    with --clover also the fermion force of a handle with a clover term (c_sw = 1)."""
     import torch
 
     import paper_2302_00850_gb300 as cola
@@ -784,8 +785,14 @@ def run_gauge_only(args):
     for _ in range(args.reps):
         cola.gauge_force(g, 5.6)
         cola.link_update(g, u, mom, 0.01)
+    if args.clover:
+        x = torch.from_numpy(synth.gaussian_spinor(dims, synth.seed_for(5, 2))).to(dev)
+        y = torch.from_numpy(synth.gaussian_spinor(dims, synth.seed_for(5, 3))).to(dev)
+        g.attach_clover(1.0)
+        for _ in range(args.reps):
+            cola.fermion_force(g, x, y)
     torch.cuda.synchronize()
-    print(json.dumps({"gauge_only": args.lattice, "reps": args.reps}))
+    print(json.dumps({"gauge_only": args.lattice, "reps": args.reps, "clover_force": bool(args.clover)}))
 
 
 def run_solve_only(args):
@@ -816,7 +823,8 @@ def main():
     ap.add_argument("--dslash-only", action="store_true", help="run chained parity Dslash applies and exit")
     ap.add_argument("--gauge-only", action="store_true", help="run gauge-force and link-update kernels and exit")
     ap.add_argument("--prec", default="f16")
-    ap.add_argument("--clover", action="store_true", help="with --dslash-only: the clover normal operator")
+    ap.add_argument("--clover", action="store_true",
+                    help="with --dslash-only: the clover normal operator; with --gauge-only: also the clover force")
     ap.add_argument("--recon", type=int, default=12)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
