@@ -21,7 +21,7 @@ definitions, each stated where it is coded:
   force.py   the fermion force dS/dU of S = phi^dag (D^dag D)^-1 phi
   clover.py  the clover (Sheikholeslami-Wohlert) term A(x), D_sw = A - kappa H,
              its even-odd Schur operator A_ee - kappa^2 H_eo A_oo^-1 H_oe and
-             the clover term's part of the fermion force
+             the clover term's parts of the fermion force and of the raw link gradient
   hmc.py     Wilson gauge action and force, momenta, leapfrog and Omelyan
              integrators, the Hamiltonian and the Metropolis step
   eig.py     the lowest eigenpairs of D^dag D and Mhat^dag Mhat (dense and
@@ -37,7 +37,8 @@ phi = D^dag eta; for the clover term the unit-gauge reduction, a constant
 abelian field in closed form, the weak-field lattice curl, gauge covariance,
 dense Schur identities and the tree-level cancellation of the Wilson lift of
 Landau zero modes (which fixes its sign), and its force against finite
-differences of the bilinear -2 Re Y^dag D_sw X and of the action; for HMC the gauge force against
+differences of the bilinear -2 Re Y^dag D_sw X and of the action, and its
+raw link gradient against finite differences of link entries; for HMC the gauge force against
 finite differences of the action, exact free motion, reversibility and the
 second-order scaling of dH (with and without the clover term); for the eigenmodes the closed-form free-field
 spectra of D^dag D and Mhat^dag Mhat (derived in eig.py).  Every function

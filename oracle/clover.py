@@ -314,3 +314,32 @@ def clover_force_links(u, x_field, y_field, kappa, csw, links):
                             sign = 1.0
                         out[n] += sign * 0.25 * kappa * csw * np.einsum("kab,ba->k", T_GEN, w).real
     return out
+
+
+def dirac_link_grad_clover(u, psi, g, kappa, csw):
+    """Clover part of the raw complex link gradient of a real loss through
+    y = D_sw psi, in PyTorch's convention (grad = 2 dL/d conj(U), U a general
+    complex matrix), given g = dL/dy in that convention: [4, Lt, Lz, Ly, Lx, 3, 3].
+
+    dL = Re g^dag dA psi = -(kappa c_sw / 8) sum_x sum_{m<n} Im Tr[dQ_mn Gam_mn]
+    with Gam from (X, Y) = (psi, g) as in clover_force_gamma.  A factor U of a
+    leaf B U C gives Im Tr[dU M], M = C Gam B, whose gradient is -i c M^dag;
+    a factor U^dag gives Im Tr[dU^dag M], gradient +i c M; c = kappa c_sw / 8.
+    The hopping part is force.dirac_link_grad.
+    """
+    out = np.zeros(u.shape, dtype=np.complex128)
+    gam = clover_force_gamma(psi, g)
+    c = kappa * csw / 8.0
+    for (mu, nu), gm in gam.items():
+        for path in LEAF_PATHS:
+            mats = []
+            for d, om, on, adj in path:
+                m = _shift2(u[mu if d == 0 else nu], mu, om, nu, on)
+                mats.append(_dag(m) if adj else m)
+            for k, (d, om, on, adj) in enumerate(path):
+                after = _mm(*mats[k + 1:]) if k < 3 else None
+                before = _mm(*mats[:k]) if k > 0 else None
+                m = _mm(*[x for x in (after, gm, before) if x is not None])
+                term = 1j * c * m if adj else -1j * c * _dag(m)
+                out[mu if d == 0 else nu] += _shift2(term, mu, -om, nu, -on)
+    return out

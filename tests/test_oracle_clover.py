@@ -16,7 +16,9 @@ Checked against what the definitions fix without re-typing them:
 - the clover force: central finite differences of -2 Re <Y, D_sw(U) X> (all
   links at once and single (link, generator) pairs) and of the action
   phi^dag (D_sw^dag D_sw)^-1 phi, zero at c_sw = 0, gauge covariance, and the
-  per-link form against the whole-lattice form.
+  per-link form against the whole-lattice form;
+- the raw link gradient of Re <w, D_sw psi> against finite differences in the
+  real and imaginary directions of single link entries.
 """
 import numpy as np
 import pytest
@@ -382,3 +384,33 @@ def test_clover_force_links_matches_whole_lattice():
     got = clv.clover_force_links(u, x, y, 0.13, 1.1, links)
     want = np.array([f[m, i] for m, i in links])
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_clover_link_gradient_against_finite_differences():
+    """grad_U of L = Re<w, D_sw psi> in PyTorch's convention (dL/dRe + i dL/dIm of each
+    link entry, U a general complex matrix): hopping plus clover parts."""
+    dims = (4, 2, 2, 4)
+    kappa, csw = 0.13, 1.4
+    bc = (np.exp(0.3j), 1.0, 1.0, -1.0)
+    u = synth.gauge_field(dims, 0.4, synth.seed_for(98, 12))
+    psi = synth.gaussian_spinor(dims, synth.seed_for(98, 13))
+    w = synth.gaussian_spinor(dims, synth.seed_for(98, 14))
+
+    def loss(uu):
+        return float(np.real(np.sum(np.conj(w) * clv.dirac_clover(uu, psi, kappa, bc, csw))))
+
+    g = oracle.dirac_link_grad(u, psi, w, kappa, bc) + clv.dirac_link_grad_clover(u, psi, w, kappa, csw)
+    h = 1e-6
+    rng = np.random.default_rng(15)
+    idxs = [(0, 3, 1, 1, 3, 0, 2), (3, 0, 0, 0, 0, 1, 1)]
+    idxs += [tuple(int(rng.integers(n)) for n in u.shape) for _ in range(6)]
+    for idx in idxs:
+        for direction, part in ((1.0, "re"), (1j, "im")):
+            up = u.copy()
+            um = u.copy()
+            up[idx] += h * direction
+            um[idx] -= h * direction
+            d = (loss(up) - loss(um)) / (2 * h)
+            want = g[idx].real if part == "re" else g[idx].imag
+            assert abs(d - want) < 1e-8 * max(1.0, abs(want)), (idx, part, d, want)
+    assert np.all(clv.dirac_link_grad_clover(u, psi, w, kappa, 0.0) == 0)
