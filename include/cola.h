@@ -166,9 +166,8 @@ cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const void *in, in
  * the handle holds (72 reals per site each; FP16 without a scale).  From then
  * on cola_dirac_apply, cola_mdagm_apply(_noalloc) and cola_cg_solve(_batched)
  * use the clover operator, cola_gauge_update rebuilds the term for the new
- * links, cola_fermion_force adds the clover term's force and
- * cola_hmc_trajectory integrates the clover action; cola_dirac_link_grad
- * returns COLA_ERR_UNSUPPORTED (it differentiates the hopping term only).
+ * links, cola_fermion_force and cola_dirac_link_grad add the clover term's
+ * parts, and cola_hmc_trajectory integrates the clover action.
  * cola_dslash_apply stays the bare hopping term.  csw = 0 removes the term.
  * The call waits for its stream (it reads back a pivot flag): it returns
  * COLA_ERR_BREAKDOWN, and leaves the handle without a clover term, if some
@@ -297,7 +296,13 @@ cola_status cola_fermion_force(cola_gauge g, double *force_dev, const void *X_de
  * convention grad = 2 dL/d conj(U) (PyTorch's), given g = that gradient on y:
  * grad_U_mu(x)_ab = -kappa conj(ph) [ sum_s g(x)_sa conj([(1-gamma_mu) psi(x+mu)]_sb)
  *                                    + sum_s [(1+gamma_mu) psi(x)]_sa conj(g(x+mu)_sb) ],
- * ph the link's boundary phase.  Canonical FP64 in and out ([4][V][3][3]). */
+ * ph the link's boundary phase.  Canonical FP64 in and out ([4][V][3][3]).
+ * With a clover term (D = A - kappa H) the clover part is added: with Gam
+ * built from (X, Y) = (psi, g) as for cola_fermion_force, dL = Re g^dag dA psi
+ * = -(kappa c_sw / 8) sum_x sum_{mu<nu} Im Tr[dQ_munu Gam_munu], and a factor
+ * U (U^dag) of a leaf contributes -i (kappa c_sw / 8) M^dag (+i (kappa c_sw / 8) M),
+ * M the rest of the leaf with Gam inserted; the links without boundary
+ * phases; 384 bytes of handle workspace per site. */
 cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void *psi_dev,
                                  const void *gy_dev, cudaStream_t stream);
 

@@ -312,7 +312,8 @@ def fermion_force(g: Gauge, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
 
 
 def dirac_link_grad(g: Gauge, psi: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
-    """Raw complex link gradient (torch convention) of a real loss through y = D psi, given dL/dy."""
+    """Raw complex link gradient (torch convention) of a real loss through y = D psi, given dL/dy
+    (with a clover term attached, D = A - kappa H and the clover part is included)."""
     lx, ly, lz, lt = g.dims
     out = torch.empty((4, lt, lz, ly, lx, 3, 3), dtype=torch.complex128, device=g.device)
     check(g.lib.cola_dirac_link_grad(g.handle, _ptr(out), _complex_field(psi, g.volume * 12, "psi"),

@@ -26,8 +26,8 @@ def _gauge(links, dims, kappa, bc, precisions=("f64",)):
 class DiracOp(torch.autograd.Function):
     """y = D[U] psi on canonical complex128 fields (csw != 0: D = A - kappa H).
 
-    With a clover term only the gradient with respect to psi is available
-    (the link gradient of the clover term is not implemented and raises).
+    Gradients with respect to psi (D^dag gy) and to the links (the raw complex
+    gradient, hopping and clover parts) in PyTorch's convention.
     """
 
     @staticmethod

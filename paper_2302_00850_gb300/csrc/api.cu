@@ -247,11 +247,6 @@ static cola_status check_rhs(int nrhs) {
     return COLA_OK;
 }
 
-static cola_status clover_unsupported(const char *what) {
-    set_error(std::string(what) + " differentiates the hopping term only; the handle has a clover term");
-    return COLA_ERR_UNSUPPORTED;
-}
-
 extern "C" {
 
 const char *cola_last_error(void) { return g_last_error.c_str(); }
@@ -439,9 +434,15 @@ cola_status cola_dirac_link_grad(cola_gauge g, void *grad_links_dev, const void 
                                  cudaStream_t stream) {
     TraceRange trace_("cola_dirac_link_grad");
     if (!g || !grad_links_dev || !psi_dev || !gy_dev) return arg_error("null argument to cola_dirac_link_grad");
-    if (g->csw != 0.0) return clover_unsupported("cola_dirac_link_grad");
-    return cuda_check(launch_link_grad(g->geom, g->lat.kappa, grad_links_dev, psi_dev, gy_dev, stream),
-                      "link gradient launch");
+    COLA_CUDA(launch_link_grad(g->geom, g->lat.kappa, grad_links_dev, psi_dev, gy_dev, stream),
+              "link gradient launch");
+    if (g->csw == 0.0) return COLA_OK;
+    COLA_TRY(check_prec(g, COLA_F64));
+    void *scratch;
+    COLA_TRY(ws_slot(g, cola_gauge_s::kSlotCloverForce, clover_force_scratch_bytes(g->geom), &scratch));
+    return cuda_check(launch_clover_link_grad(g->geom, g->links[COLA_F64], g->recon[COLA_F64], g->lat.kappa, g->csw,
+                                              psi_dev, gy_dev, grad_links_dev, scratch, stream),
+                      "clover link gradient launch");
 }
 
 }  // extern "C"

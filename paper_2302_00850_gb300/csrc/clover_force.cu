@@ -22,6 +22,12 @@
 //   dS/deps^a = (kappa c_sw / 4) Re Tr[T^a Z]   (U -> (1 + i eps T^a) U).
 // Two kernels, FP64 throughout: Gam on every site (six planes, eight reals
 // each: Gam is Hermitian and traceless), then one thread per link.
+//
+// The same sums give the clover part of the raw complex link gradient of a
+// real loss through y = D psi (PyTorch's convention, grad = 2 dL/d conj(U)),
+// with (X, Y) = (psi, dL/dy): dL = Re gy^dag dA psi is -1/2 of the form above,
+// and a factor U (U^dag) of Im Tr[dU M] (Im Tr[dU^dag M]) has gradient -i M^dag
+// (+i M), so per link grad = -i (kappa c_sw / 8) (S+^dag - S-).
 #include "cola_impl.h"
 
 namespace cola {
@@ -170,9 +176,11 @@ __device__ __forceinline__ void gam_off(const Geom &g, const double *gam, int pl
     gam_at(g, gam, plane, sign, p, m);
 }
 
-template <int RECON>
+// GRAD = false: out is the force [4][V][8] (reals), coef multiplies Re Tr[lambda^a Z].
+// GRAD = true: out is the raw link gradient [4][V][3][3] (double2), out += -i coef (S+^dag - S-).
+template <int RECON, bool GRAD>
 __global__ void __launch_bounds__(128) clover_force_kernel(const Geom g, const char *links, size_t dir_stride,
-                                                           const double *gam, double *out, double coef,
+                                                           const double *gam, void *out, double coef,
                                                            int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int mu = blockIdx.y;
@@ -228,6 +236,23 @@ __global__ void __launch_bounds__(128) clover_force_kernel(const Geom g, const c
         gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                     // G(y+mu)
         mac3(sm, a, gm);                                                       // + M1 M2 M3 G(y+mu)
     }
+    if constexpr (GRAD) {
+        double2 *o = static_cast<double2 *>(out) + ((size_t)mu * g.V + i) * 9;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const C64 v = {sp[3 * b + a].re - sm[3 * a + b].re, -sp[3 * b + a].im - sm[3 * a + b].im};
+                double2 r = make_double2(coef * v.im, -coef * v.re);  // -i coef v
+                if (accumulate) {
+                    const double2 p = o[3 * a + b];
+                    r.x += p.x;
+                    r.y += p.y;
+                }
+                o[3 * a + b] = r;
+            }
+        return;
+    }
     // Z = U S+ - S- U^dag; F^a = coef Re Tr[lambda^a Z] = coef Im Tr[lambda^a (i Z)]
     C64 u[9], z[9], w[9];
     link_at<RECON>(g, links, dir_stride, c, mu, u);
@@ -238,7 +263,7 @@ __global__ void __launch_bounds__(128) clover_force_kernel(const Geom g, const c
     for (int k = 0; k < 9; ++k) w[k] = {-(z[k].im - w[k].im), z[k].re - w[k].re};  // i (z - w)
     double fa[8];
     im_tr_lambda(w, fa);
-    store_force(out + ((size_t)mu * g.V + i) * 8, fa, coef, accumulate != 0);
+    store_force(static_cast<double *>(out) + ((size_t)mu * g.V + i) * 8, fa, coef, accumulate != 0);
 }
 
 }  // namespace
@@ -258,8 +283,25 @@ cudaError_t launch_clover_force(const Geom &g, const void *links_f64, int recon,
     const size_t ds = link_dir_bytes(COLA_F64, recon, g.Vh);
     // dS/deps^a = (kappa c_sw / 4) Re Tr[T^a Z] = (kappa c_sw / 8) Re Tr[lambda^a Z]
     const double c = coef * kappa * csw / 8.0;
-    if (recon == 12) clover_force_kernel<12><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
-    else clover_force_kernel<18><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
+    if (recon == 12) clover_force_kernel<12, false><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
+    else clover_force_kernel<18, false><<<grid2, block, 0, s>>>(g, l, ds, gam, force, c, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clover_link_grad(const Geom &g, const void *links_f64, int recon, double kappa, double csw,
+                                    const void *psi, const void *gy, void *grad, void *scratch, cudaStream_t s) {
+    double *gam = static_cast<double *>(scratch);
+    const dim3 block(128), grid1((g.V + 127) / 128), grid2((g.V + 127) / 128, 4);
+    clover_gamma_kernel<<<grid1, block, 0, s>>>(g, clover_sigma(), static_cast<const double2 *>(psi),
+                                                static_cast<const double2 *>(gy), gam);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const char *l = static_cast<const char *>(links_f64);
+    const size_t ds = link_dir_bytes(COLA_F64, recon, g.Vh);
+    // per link: grad += -i (kappa c_sw / 8) (S+^dag - S-)
+    const double c = kappa * csw / 8.0;
+    if (recon == 12) clover_force_kernel<12, true><<<grid2, block, 0, s>>>(g, l, ds, gam, grad, c, 1);
+    else clover_force_kernel<18, true><<<grid2, block, 0, s>>>(g, l, ds, gam, grad, c, 1);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,11 @@ size_t clover_force_scratch_bytes(const Geom &g);
 cudaError_t launch_clover_force(const Geom &g, const void *links_f64, int recon, double kappa, double csw,
                                 const void *X, const void *Y, double *force, double coef, bool accumulate,
                                 void *scratch, cudaStream_t s);
+// grad += the clover term's part of the raw link gradient (PyTorch's
+// convention, canonical [4][V][3][3] complex) of a real loss through
+// y = D psi, given gy = dL/dy; same scratch as launch_clover_force.
+cudaError_t launch_clover_link_grad(const Geom &g, const void *links_f64, int recon, double kappa, double csw,
+                                    const void *psi, const void *gy, void *grad, void *scratch, cudaStream_t s);
 // out_p = C_p in_p on the parities of parity_mask (1 even, 2 odd, 3 both).
 cudaError_t launch_clover_apply(int prec, const Geom &g, const void *clv, void *out, const void *in, int nrhs,
                                 int parity_mask, cudaStream_t s);

@@ -5,7 +5,7 @@ A^-1 (through their application to random spinors, every parity and
 precision), the clover Dirac operator D = A - kappa H and its adjoint, the
 even-odd and whole-lattice normal operators, solves whose true residual the
 oracle recomputes, multi-RHS and batched solves, gauge updates, detaching,
-and the calls that refuse a clover handle.  Tolerances as for the Wilson
+autograd through the clover operator, and the FP64 links the term needs.  Tolerances as for the Wilson
 operator: 1e-13 (FP64), 1e-6 (FP32 storage), 2e-3 (FP16 storage).
 """
 import numpy as np
@@ -235,19 +235,16 @@ def test_gauge_update_rebuilds_and_detach_restores(cola):
         cola.apply_clover(g, to_dev(psi))
 
 
-def test_calls_that_refuse_a_clover_handle(cola):
+def test_clover_needs_fp64_links(cola):
     dims = (4, 4, 4, 4)
     u, psi = lattice_inputs(dims, config=72)
-    g = clover_gauge(cola, u, dims)
-    with pytest.raises(cola.ColaError, match="clover"):
-        cola.dirac_link_grad(g, to_dev(psi), to_dev(psi))
     g32 = cola.Gauge(to_dev(u), dims, KAPPA, BC_AP, precisions=("f32",))
     with pytest.raises(cola.ColaError, match="FP64"):
         g32.attach_clover(CSW)
     assert g32.csw == 0.0
 
 
-def test_dirac_op_autograd_input_gradient_with_clover(cola):
+def test_dirac_op_autograd_gradients_with_clover(cola):
     import torch
 
     dims = (4, 4, 2, 4)
@@ -260,8 +257,9 @@ def test_dirac_op_autograd_input_gradient_with_clover(cola):
     assert rel_err(gp.cpu().numpy(), ocl.dirac_clover_dag(u, gy, KAPPA, BC_AP, CSW)) < 1e-13
     lk = to_dev(u).requires_grad_(True)
     y = cola.DiracOp.apply(lk, to_dev(psi), dims, KAPPA, BC_AP, CSW)
-    with pytest.raises(cola.ColaError, match="clover"):
-        torch.autograd.grad(y, lk, to_dev(gy))
+    (gl,) = torch.autograd.grad(y, lk, to_dev(gy))
+    want = oracle.dirac_link_grad(u, psi, gy, KAPPA, BC_AP) + ocl.dirac_link_grad_clover(u, psi, gy, KAPPA, CSW)
+    assert rel_err(gl.cpu().numpy(), want) < 1e-13
 
 
 def test_multishift_and_eigensolver_on_a_clover_handle(cola):

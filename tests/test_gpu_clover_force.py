@@ -4,7 +4,8 @@ The fermion force of a handle with a clover term (hopping part plus clover
 part) element by element against the oracle on lattices with extents of 2
 (links met twice by one plaquette), anisotropic extents and both link
 reconstructions; the same force at 24^3x48 on sampled links against the
-oracle's per-link form; whole clover HMC trajectories (links, momenta, dH)
+oracle's per-link form; the raw link gradient of the clover operator
+against the oracle; whole clover HMC trajectories (links, momenta, dH)
 against the oracle's trajectory; and on the device the second-order scaling
 of dH that only the correct clover force gives.
 """
@@ -56,6 +57,20 @@ def test_clover_force_matches_oracle(cola, dims, recon):
     g.attach_clover(0.0)
     f0 = cola.fermion_force(g, to_dev(x), to_dev(y)).cpu().numpy()
     assert rel_err(f - f0, ocl.clover_force_coeffs(u, x, y, KAPPA, CSW)) < 1e-12
+
+
+@pytest.mark.parametrize("dims,recon", [((2, 2, 2, 2), 18), ((4, 6, 2, 8), 12)])
+def test_clover_link_grad_matches_oracle(cola, dims, recon):
+    """Raw complex link gradient (PyTorch's convention) of Re <gy, D_sw psi>: hopping plus clover parts."""
+    bc = (1.0, np.exp(0.5j), 1.0, -1.0)
+    u = synth.gauge_field(dims, 0.4, synth.seed_for(99, 13))
+    psi = synth.gaussian_spinor(dims, synth.seed_for(99, 14))
+    gy = synth.gaussian_spinor(dims, synth.seed_for(99, 15))
+    g = cola.Gauge(to_dev(u), dims, KAPPA, bc, precisions=("f64",), recon={"f64": recon})
+    g.attach_clover(CSW)
+    got = cola.dirac_link_grad(g, to_dev(psi), to_dev(gy)).cpu().numpy()
+    want = oracle.dirac_link_grad(u, psi, gy, KAPPA, bc) + ocl.dirac_link_grad_clover(u, psi, gy, KAPPA, CSW)
+    assert rel_err(got, want) < 1e-13
 
 
 def test_clover_force_full_size_sampled(cola):
