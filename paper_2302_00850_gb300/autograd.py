@@ -57,11 +57,13 @@ def _solve(g, rhs, tol, inner):
 
 
 class SolveNormal(torch.autograd.Function):
-    """X = (D^dag D)^-1 phi on the whole lattice."""
+    """X = (D^dag D)^-1 phi on the whole lattice (csw != 0: D = A - kappa H)."""
 
     @staticmethod
-    def forward(ctx, links, phi, dims, kappa, bc, tol=1e-12, inner="f32"):
+    def forward(ctx, links, phi, dims, kappa, bc, tol=1e-12, inner="f32", csw=0.0):
         g = _gauge(links, dims, kappa, bc, precisions=("f64", "f32") if inner != "f64" else ("f64",))
+        if csw:
+            g.attach_clover(csw)
         x, _ = _solve(g, phi.detach().contiguous(), tol, inner)
         ctx.save_for_backward(x)
         ctx.g, ctx.tol, ctx.inner = g, tol, inner
@@ -77,15 +79,17 @@ class SolveNormal(torch.autograd.Function):
             y = apply_dirac(g, x)
             w = apply_dirac(g, z)
             grad_links = -(dirac_link_grad(g, z, y) + dirac_link_grad(g, x, w))
-        return grad_links, z, None, None, None, None, None
+        return grad_links, z, None, None, None, None, None, None
 
 
 class PseudofermionAction(torch.autograd.Function):
-    """S = phi^dag (D^dag D)^-1 phi (real); dS/dU is the fermion force."""
+    """S = phi^dag (D^dag D)^-1 phi (real; csw != 0: D = A - kappa H); dS/dU is the fermion force."""
 
     @staticmethod
-    def forward(ctx, links, phi, dims, kappa, bc, tol=1e-12, inner="f32"):
+    def forward(ctx, links, phi, dims, kappa, bc, tol=1e-12, inner="f32", csw=0.0):
         g = _gauge(links, dims, kappa, bc, precisions=("f64", "f32") if inner != "f64" else ("f64",))
+        if csw:
+            g.attach_clover(csw)
         x, _ = _solve(g, phi.detach().contiguous(), tol, inner)
         ctx.save_for_backward(x)
         ctx.g = g
@@ -101,4 +105,4 @@ class PseudofermionAction(torch.autograd.Function):
             grad_links = -2.0 * gs * dirac_link_grad(g, x, y)
         if ctx.needs_input_grad[1]:
             grad_phi = 2.0 * gs * x
-        return grad_links, grad_phi, None, None, None, None, None
+        return grad_links, grad_phi, None, None, None, None, None, None

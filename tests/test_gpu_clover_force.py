@@ -73,6 +73,41 @@ def test_clover_link_grad_matches_oracle(cola, dims, recon):
     assert rel_err(got, want) < 1e-13
 
 
+def test_clover_autograd_action_gradient_is_the_force(cola):
+    """dS/dU from PseudofermionAction.backward with the clover term (the link-gradient kernel)
+    projects onto the clover fermion force (the force kernel), F^a = Re<G, i T^a U>; and the
+    link gradient of Re <w, X> through SolveNormal against the oracle's solves and gradients."""
+    import torch
+
+    dims = (4, 4, 2, 4)
+    kappa = 0.124
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(99, 16))
+    phi = synth.gaussian_spinor(dims, synth.seed_for(99, 17))
+    links = to_dev(u).requires_grad_(True)
+    S = cola.PseudofermionAction.apply(links, to_dev(phi), dims, kappa, BC_AP, 1e-13, "f32", CSW)
+    S.backward()
+    G = links.grad.cpu().numpy()
+    g = cola.Gauge(to_dev(u), dims, kappa, BC_AP, precisions=("f64",))
+    g.attach_clover(CSW)
+    X, _ = cola.cg_solve(g, to_dev(phi), tol=1e-13, op="full", inner="f64")
+    F = cola.fermion_force(g, X, cola.apply_dirac(g, X)).cpu().numpy()
+    tu = np.einsum("kab,...bc->...kac", oracle.T_GEN, u)
+    proj = np.real(np.einsum("...ab,...kab->...k", G.conj(), 1j * tu))
+    assert rel_err(proj, F) < 1e-9
+    w = synth.gaussian_spinor(dims, synth.seed_for(99, 18))
+    links = to_dev(u).requires_grad_(True)
+    Xs = cola.SolveNormal.apply(links, to_dev(phi), dims, kappa, BC_AP, 1e-13, "f64", CSW)
+    torch.real(torch.vdot(to_dev(w).reshape(-1), Xs.reshape(-1))).backward()
+    x = ocl.solve_normal_full_clover(u, phi, kappa, BC_AP, CSW, tol=1e-13)[0]
+    z = ocl.solve_normal_full_clover(u, w, kappa, BC_AP, CSW, tol=1e-13)[0]
+    y, wz = ocl.dirac_clover(u, x, kappa, BC_AP, CSW), ocl.dirac_clover(u, z, kappa, BC_AP, CSW)
+
+    def grad(psi, gy):
+        return oracle.dirac_link_grad(u, psi, gy, kappa, BC_AP) + ocl.dirac_link_grad_clover(u, psi, gy, kappa, CSW)
+
+    assert rel_err(links.grad.cpu().numpy(), -(grad(z, y) + grad(x, wz))) < 1e-9
+
+
 def test_clover_force_full_size_sampled(cola):
     """24^3x48 (the HMC benchmark's lattice), 1500 sampled links and the corners."""
     dims = (24, 24, 24, 48)
