@@ -35,8 +35,10 @@
  *    cola_gauge_destroy.
  *  - All work is ordered on the given stream; calls return after enqueuing,
  *    except those that report results to the host (the solvers, the
- *    eigensolver, the HMC trajectory, cola_plaquette, cola_clover_attach),
- *    which synchronise the stream.
+ *    eigensolver, the HMC trajectory, cola_plaquette, cola_clover_attach,
+ *    and cola_gauge_update / cola_link_update on a handle with a clover term,
+ *    which rebuild it and read back its pivot flag), which synchronise the
+ *    stream.  A call that first needs handle workspace allocates it then.
  *  - A handle is not thread-safe: its workspace is reused by every call, so
  *    calls on one handle must be ordered (one stream, or synchronised).
  *  - Errors are returned as cola_status codes; nothing aborts.  The message
