@@ -379,6 +379,16 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
 /* Thread-local message describing the last error returned on this thread. */
 const char *cola_last_error(void);
 
+/* Debug builds only (libcola compiled with -DCOLA_BOUNDS): every neighbour,
+ * link and site index the kernels compute is checked against its extent; an
+ * index out of range is counted, the kernel source line of the first one is
+ * recorded, and the access is redirected to index 0 (no fault, wrong result).
+ * Waits for the device, then returns in *count (host) the number of
+ * violations since the last reset and in *first_line (host) that line, 0 if
+ * none; reset != 0 zeroes the counters.  A default build returns
+ * COLA_ERR_UNSUPPORTED. */
+cola_status cola_debug_bounds(unsigned long long *count, int *first_line, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,8 +11,8 @@ hand-written sm_103a kernels (include/cola.h), and this thin torch binding.
     g.attach_clover(1.0)        # D = A - kappa H from here on
 """
 from .api import (  # noqa: F401
-    ColaError, EigInfo, Gauge, HmcInfo, SolveInfo, apply_clover, apply_dirac, cg_solve, cg_solve_batched, clover, dirac,
-    dirac_link_grad, dslash, eig_lowest, fermion_force, gauge_force, hmc_trajectory, link_update, mdagm, multishift_solve,
+    ColaError, EigInfo, Gauge, HmcInfo, SolveInfo, apply_clover, apply_dirac, cg_solve, cg_solve_batched, clover,
+    debug_bounds, dirac, dirac_link_grad, dslash, eig_lowest, fermion_force, gauge_force, hmc_trajectory, link_update, mdagm, multishift_solve,
     pack, plaquette, unpack, F16, F32, F64, OP_EO, OP_FULL, SYS_DIRAC, SYS_NORMAL,
 )
 from .autograd import DiracOp, PseudofermionAction, SolveNormal  # noqa: F401

@@ -11,7 +11,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libcola.so")
+# COLA_LIB selects another in-tree build, e.g. the bounds-checking debug build
+# (python -m paper_2302_00850_gb300.build --bounds writes _build_bounds/libcola.so)
+LIB_PATH = os.environ.get("COLA_LIB") or os.path.join(_PKG, "_build", "libcola.so")
 
 COLA_OK = 0
 STATUS_NAMES = {
@@ -106,6 +108,7 @@ SIGNATURES = {
     "cola_link_update": (_st, [_vp, _vp, _vp, _d, _vp]),
     "cola_hmc_trajectory": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(HmcParams), ctypes.POINTER(HmcInfo), _vp]),
     "cola_last_error": (ctypes.c_char_p, []),
+    "cola_debug_bounds": (_st, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(_i), _i]),
 }
 
 _lib = None

@@ -382,3 +382,13 @@ def hmc_trajectory(g: Gauge, links: torch.Tensor, mom: torch.Tensor, eta: torch.
                                     eta_p, ctypes.byref(prm), ctypes.byref(info), _stream(g.device)))
     return HmcInfo(info.dH, info.H0, info.H1, bool(info.accepted), info.plaquette, info.force_evals, info.cg_iters,
                    info.seconds)
+
+
+def debug_bounds(reset: bool = False) -> tuple[int, int]:
+    """(violations, kernel source line of the first) of the bounds-checking debug build
+    (COLA_LIB=.../_build_bounds/libcola.so); waits for the device; reset zeroes the counters.
+    A default build raises ColaError (COLA_ERR_UNSUPPORTED)."""
+    lib = _lib.load()
+    count, line = ctypes.c_ulonglong(0), ctypes.c_int(0)
+    check(lib.cola_debug_bounds(ctypes.byref(count), ctypes.byref(line), int(bool(reset))))
+    return int(count.value), int(line.value)

@@ -3,7 +3,8 @@
 Each CUDA translation unit is compiled in its own nvcc process (in parallel)
 and the objects are linked into paper_2302_00850_gb300/_build/libcola.so with
 the CUDA runtime linked statically, so the library depends only on the
-driver.  Usage: python -m paper_2302_00850_gb300.build [--force]
+driver.  Usage: python -m paper_2302_00850_gb300.build [--force] [--bounds]
+(--bounds: the debug build with index checks, in _build_bounds/).
 """
 from __future__ import annotations
 
@@ -55,6 +56,15 @@ def _compile(src: str, extra, out_dir: str) -> str:
     return obj
 
 
+BOUNDS_DIR = os.path.join(PKG, "_build_bounds")
+
+
+def build_bounds(force: bool = False) -> str:
+    """The debug build with every computed index checked (-DCOLA_BOUNDS), in _build_bounds/;
+    load it with COLA_LIB=<returned path>."""
+    return build(force=force, extra=["-DCOLA_BOUNDS"], out_dir=BOUNDS_DIR)
+
+
 def build(force: bool = False, verbose: bool = False, extra=(), out_dir: str | None = None) -> str:
     """Compile every translation unit and link libcola.so; returns its path.
 
@@ -79,5 +89,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), out_dir: str | N
 
 
 if __name__ == "__main__":
-    path = build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    if "--bounds" in sys.argv:
+        path = build_bounds(force="--force" in sys.argv)
+    else:
+        path = build(force="--force" in sys.argv, verbose="-v" in sys.argv)
     print(path)

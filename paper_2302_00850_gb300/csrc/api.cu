@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "cola_impl.h"
 
@@ -33,6 +34,18 @@ void log_line(const char *fmt, ...) {
 
 TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
 TraceRange::~TraceRange() { nvtxRangePop(); }
+
+#ifdef COLA_BOUNDS
+// readers of the per-translation-unit bounds counters, registered at load time
+static std::vector<BoundsReader> &bounds_readers() {
+    static std::vector<BoundsReader> r;
+    return r;
+}
+bool register_bounds_reader(BoundsReader r) {
+    bounds_readers().push_back(r);
+    return true;
+}
+#endif
 
 static thread_local std::string g_last_error;
 
@@ -250,6 +263,27 @@ static cola_status check_rhs(int nrhs) {
 extern "C" {
 
 const char *cola_last_error(void) { return g_last_error.c_str(); }
+
+cola_status cola_debug_bounds(unsigned long long *count, int *first_line, int reset) {
+    if (!count || !first_line) return arg_error("null argument to cola_debug_bounds");
+    *count = 0;
+    *first_line = 0;
+#ifdef COLA_BOUNDS
+    COLA_CUDA(cudaDeviceSynchronize(), "bounds counters");
+    for (BoundsReader r : bounds_readers()) {
+        unsigned long long c = 0;
+        int line = 0;
+        COLA_CUDA(r(&c, &line, reset != 0), "bounds counters");
+        if (c && !*first_line) *first_line = line;
+        *count += c;
+    }
+    return COLA_OK;
+#else
+    (void)reset;
+    set_error("libcola was built without COLA_BOUNDS: no bounds checks to report");
+    return COLA_ERR_UNSUPPORTED;
+#endif
+}
 
 size_t cola_spinor_bytes(const cola_lattice *lat, cola_prec prec, int nrhs) {
     if (check_lattice(lat) != COLA_OK || prec < 0 || prec > 2 || nrhs < 1) return 0;

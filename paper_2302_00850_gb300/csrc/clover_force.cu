@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(128) clover_gamma_kernel(const Geom g, const C
 __device__ __forceinline__ int lex_site(const Geom &g, const int (&p)[4]) {
     const int x = wrap_coord(p[0], g.L[0]), y = wrap_coord(p[1], g.L[1]);
     const int z = wrap_coord(p[2], g.L[2]), t = wrap_coord(p[3], g.L[3]);
-    return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+    return COLA_BOUND(x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t)), g.V);
 }
 
 // G = sign Gam_plane at the site with coordinates p (wrapped)

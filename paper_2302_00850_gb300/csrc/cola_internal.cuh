@@ -11,6 +11,48 @@
 
 namespace cola {
 
+// ----------------------------------------------------------- bounds checks --
+// A debug build (-DCOLA_BOUNDS) checks every computed neighbour, link and site
+// index against its extent before it is used.  An index out of range is
+// counted, the source line of the first one is recorded, and the access is
+// redirected to index 0 so that nothing faults; cola_debug_bounds() reports
+// the count.  Each translation unit keeps its own counter (device variables
+// have internal linkage without relocatable device code) and registers a
+// reader with the library at load time.  Default builds compile the checks
+// away: COLA_BOUND(i, n) is then the bare index.
+#ifdef COLA_BOUNDS
+static __device__ unsigned long long g_bounds_count;
+static __device__ int g_bounds_line;
+
+__device__ __forceinline__ int bound_check(long long i, long long n, int line) {
+    if (i < 0 || i >= n) {
+        if (atomicAdd(&g_bounds_count, 1ull) == 0ull) g_bounds_line = line;
+        return 0;
+    }
+    return (int)i;
+}
+#define COLA_BOUND(i, n) ::cola::bound_check((long long)(i), (long long)(n), __LINE__)
+
+using BoundsReader = cudaError_t (*)(unsigned long long *count, int *line, bool reset);
+bool register_bounds_reader(BoundsReader r);
+
+// this translation unit's counter and first line (reset: zero them after reading)
+static cudaError_t bounds_read_local(unsigned long long *count, int *line, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_bounds_count, sizeof(*count));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(line, g_bounds_line, sizeof(*line));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long zc = 0;
+        const int zl = 0;
+        e = cudaMemcpyToSymbol(g_bounds_count, &zc, sizeof(zc));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_line, &zl, sizeof(zl));
+    }
+    return e;
+}
+[[maybe_unused]] static const bool g_bounds_registered = register_bounds_reader(&bounds_read_local);
+#else
+#define COLA_BOUND(i, n) (i)
+#endif
+
 // ---------------------------------------------------------------- geometry --
 // Division by a fixed divisor d through a multiply-high (Granlund and
 // Montgomery, "Division by invariant integers using multiplication", 1994):
@@ -78,13 +120,13 @@ __device__ __forceinline__ int nbr_cb(const Geom &g, const Coord &c, int cb) {
         int xn = c.x + DIR;
         if (DIR > 0 && xn == g.L[0]) xn = 0;
         if (DIR < 0 && xn < 0) xn = g.L[0] - 1;
-        return cb - (c.x >> 1) + (xn >> 1);
+        return COLA_BOUND(cb - (c.x >> 1) + (xn >> 1), g.Vh);
     } else {
         const int coord = (MU == 1) ? c.y : (MU == 2) ? c.z : c.t;
         const int L = g.L[MU];
         const int s = g.stride[MU];
-        if (DIR > 0) return (coord == L - 1) ? cb - (L - 1) * s : cb + s;
-        return (coord == 0) ? cb + (L - 1) * s : cb - s;
+        if (DIR > 0) return COLA_BOUND((coord == L - 1) ? cb - (L - 1) * s : cb + s, g.Vh);
+        return COLA_BOUND((coord == 0) ? cb + (L - 1) * s : cb - s, g.Vh);
     }
 }
 
@@ -365,7 +407,7 @@ __device__ __forceinline__ void link_at(const Geom &g, const char *links, size_t
     const int x = wrap_coord(p[0], g.L[0]), y = wrap_coord(p[1], g.L[1]);
     const int z = wrap_coord(p[2], g.L[2]), t = wrap_coord(p[3], g.L[3]);
     const int par = (x + y + z + t) & 1;
-    const int cb = (x >> 1) + g.Lxh * (y + g.L[1] * (z + g.L[2] * t));
+    const int cb = COLA_BOUND((x >> 1) + g.Lxh * (y + g.L[1] * (z + g.L[2] * t)), g.Vh);
     LinkIO<COLA_F64, RECON>::load(links + (size_t)(4 * par + mu) * link_dir_stride, g.Vh, cb, u);
 }
 

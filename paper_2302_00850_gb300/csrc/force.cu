@@ -74,7 +74,7 @@ __device__ __forceinline__ void site_coords(const Geom &g, int i, int (&c)[4]) {
 __device__ __forceinline__ int site_fwd(const Geom &g, int i, const int (&c)[4], int mu) {
     int step = 1;
     for (int k = 0; k < mu; ++k) step *= g.L[k];
-    return c[mu] == g.L[mu] - 1 ? i - (g.L[mu] - 1) * step : i + step;
+    return COLA_BOUND(c[mu] == g.L[mu] - 1 ? i - (g.L[mu] - 1) * step : i + step, g.V);
 }
 
 template <int MU, int RECON>

@@ -17,7 +17,7 @@ __device__ __forceinline__ void site_parity_cb(const Geom &g, int i, int &par, i
     int z = r % g.L[2];
     int t = r / g.L[2];
     par = (x + y + z + t) & 1;
-    cb = i >> 1;
+    cb = COLA_BOUND(i >> 1, g.Vh);
 }
 
 template <int P>
