@@ -5,6 +5,8 @@
 - the gauge force against central finite differences of the action, along a
   random su(3) direction and along single (link, generator) pairs;
 - free motion (beta = 0, no fermions) is U(tau) = exp(i tau P) U exactly;
+- the link exponential itself against scipy's Pade expm at large steps,
+  unitarity, unit determinant and the one-parameter group law;
 - reversibility: integrating back with -p returns the start (leapfrog and
   Omelyan, with and without fermions);
 - energy conservation: dH falls by about 4 when the step halves (both
@@ -149,3 +151,24 @@ def test_clover_trajectory_reversible_and_second_order():
     assert np.max(np.abs(u0 - u)) < 1e-10 and np.max(np.abs(-p0 - p)) < 1e-9
     dh = {n: hmc.trajectory(u, p, eta, beta, kappa, BC_AP, 0.5, n, "leapfrog", tol=1e-13, csw=csw)[1] for n in (4, 8)}
     assert 3.0 < dh[4] / dh[8] < 5.0, dh
+
+
+def test_link_variation_is_the_group_exponential():
+    """exp(i eps P) U with P = sum_a p^a T^a, at large eps: equal to scipy's Pade
+    expm (a different algorithm from the oracle's eigendecomposition), unitary with
+    unit determinant, and a one-parameter group (exp(i a P) exp(i b P) = exp(i (a+b) P))."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    dims = (2, 2, 2, 2)
+    u = synth.gauge_field(dims, 0.5, synth.seed_for(97, 30))
+    p = momenta(dims, 31)
+    for eps in (0.05, 0.7, 3.0):
+        got = oracle.link_variation(u, p, eps)
+        for idx in [(0, 0, 0, 0, 0), (3, 1, 1, 0, 1), (1, 0, 1, 1, 0), (2, 1, 0, 1, 1)]:
+            gen = np.einsum("k,kab->ab", p[idx], oracle.T_GEN)
+            want = scipy_linalg.expm(1j * eps * gen) @ u[idx]
+            assert np.max(np.abs(got[idx] - want)) < 1e-13, (eps, idx)
+        eye = np.einsum("...ab,...cb->...ac", got, got.conj())
+        assert np.max(np.abs(eye - np.eye(3))) < 1e-13
+        assert np.max(np.abs(np.linalg.det(got) - 1.0)) < 1e-13
+    two = oracle.link_variation(oracle.link_variation(u, p, 0.4), p, 0.9)
+    assert np.max(np.abs(two - oracle.link_variation(u, p, 1.3))) < 1e-13
