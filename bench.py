@@ -12,8 +12,11 @@ solve, 1320 flop per output site per parity apply, next to the plain FP64 CG
 on the same inputs and the isolated FP16 Dslash kernel against the HBM
 roofline.
 
---impl reference times the FP64 CPU oracle (numpy) on the same workload:
-each step is one oracle parity-Dslash apply on the 32^3x64 lattice.
+The oracle (plain numpy FP64) is timed on the host cores after the GPU
+work, on one core and on every core, per parity apply and per CG iteration
+for each workload (cpu_baseline).  --impl reference times the same oracle on
+the headline workload: each step is one parity Dslash of the 32^3x64 lattice
+over every host core.
 """
 from __future__ import annotations
 
@@ -44,14 +47,56 @@ METRIC = "Wilson Dslash GFLOP/s & HBM GB/s; mixed-vs-FP64 CG time at 1e-10 resid
 # 8 links x 24 B + input spinor 48 B + its FP32 scale + output 48 B + scale
 BYTES_PER_SITE_F16 = 8 * 24 + 52 + 52
 BYTES_PER_SITE_F32 = 8 * 48 + 96 + 96
-# FP64 peak of this part from its unit counts and clock: 152 SMs x 2 DFMA per
-# SM per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak) x 2 flop
-# x 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch from one ncu capture of each kernel at
-# 32^3x64 (profiles/dslash_f64_32x32x32x64.md, profiles/dslash_f16_32x32x32x64.md);
-# None when the kernel changed after the capture.
-NCU_TRAFFIC = {"f64": 1.6146e9, "f16": 298.8e6}
+# FP64 peak of this part derived from its unit counts and clock, reported
+# beside the measured one: 152 SMs x 2 DFMA per SM per cycle (the peak of
+# ncu's DFMA instruction counter) x 2 flop x 2.07 GHz maximum SM clock.
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch of the hopping kernel at 32^3x64 from
+# one ncu capture, with the digest of the kernel sources at capture time: the
+# figure is reported only while the sources still have that digest, else the
+# traffic is null (the kernel changed since the counters were taken).
+KERNEL_SOURCES = ["cola_internal.cuh", "cola_impl.h", "dslash_kernel.cuh", "dslash.cu"]
+NCU_TRAFFIC = {"f64": (1.6146e9, None), "f16": (298.8e6, None)}
+
+
+def kernel_source_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2302_00850_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    nbytes, digest = NCU_TRAFFIC[prec]
+    return nbytes if digest is not None and digest == kernel_source_digest() else None
+
+
+FP64_PEAK_MEASURED = [FP64_PEAK_DERIVED_TFLOPS]  # replaced by the measurement of this run
+
+
+def measure_fp64_peak(cola, dev, stream, reps=5):
+    """FP64 arithmetic rate of this GPU now: independent DFMA chains (the
+    library's probe kernel) on 8 blocks per SM, timed with CUDA events on the
+    launching stream after a warm-up launch; best of `reps` launches."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, steps = 8 * sms, 256, 4096
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    cola.api.probe_fp64_fma(out, blocks, threads, steps)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flop = cola.api.probe_fp64_fma(out, blocks, threads, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tf = flop / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        best = tf if best is None else max(best, tf)
+    return best
 
 
 def dist_env():
@@ -135,58 +180,310 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def cpu_baseline_sample(u_np, psi_np):
-    """Oracle (numpy FP64) parity Dslash on the full lattice, timed on the host."""
+# ------------------------------------------------------------ CPU oracle --
+# The oracle (plain numpy FP64) timed on the host cores, on one core and on
+# every core.  The all-core figure splits one parity apply into disjoint site
+# chunks and runs the oracle's own hop_sites on each in a process pool.  The
+# pool is started by fork from a process that has made no CUDA call (the
+# bench runs this study in a child process after its GPU work, and the
+# reference arm never touches the GPU), so the children inherit the inputs
+# without copies.
+
+# (name, lattices, link scale eps, kappa, seed config, right-hand sides per lattice)
+CPU_CONFIGS = [
+    ("4x4x4x4", [(4, 4, 4, 4)], 0.3, 0.12, 0, 1),
+    ("16x16x16x32", [(16, 16, 16, 32)], 0.3, 0.125, 1, 1),
+    ("32x32x32x64", [(32, 32, 32, 64)], 0.25, 0.1245, 2, 1),
+    ("24x24x24x48-12-point-sources", [(24, 24, 24, 48)], 0.3, 0.124, 3, 12),
+    ("batch-8^4+12^3x24+16^3x32+24^3x48-x4", [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), (24, 24, 24, 48)],
+     0.3, 0.124, 3, 4),
+]
+_CPU_FIELDS = {}  # lattice key -> (u, psi); set before the pool forks
+
+
+def _lat_key(dims):
+    return "x".join(map(str, dims))
+
+
+def _cpu_hop_chunk(task):
+    """One site chunk of a parity apply (runs in a pool worker)."""
+    import numpy as np
+
     import oracle
 
-    vh = u_np.shape[1] * u_np.shape[2] * u_np.shape[3] * u_np.shape[4] // 2
+    key, sites = task
+    u, psi = _CPU_FIELDS[key]
+    return float(np.abs(oracle.hop_sites(u, psi, BC, sites)).sum())
+
+
+def host_cpu_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+
+    return {"cpu_model": model or "unknown", "machine": platform.machine(),
+            "nproc": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()}
+
+
+def _parity_sites(dims, parity=0):
+    import numpy as np
+
+    import oracle
+
+    return np.nonzero(oracle.parity_of_sites(dims).ravel() == parity)[0].astype(np.int64)
+
+
+def _cpu_vector_ops_s(dims):
+    """One CG iteration's vector operations of the oracle's cg on one field."""
+    import numpy as np
+
+    from oracle import solve
+
+    lx, ly, lz, lt = dims
+    rng = np.random.default_rng(0)
+    shape = (lt, lz, ly, lx, 4, 3)
+    p, q, r, x = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape) for _ in range(4))
     t0 = time.perf_counter()
-    oracle.hop_block(u_np, psi_np, BC, 0)
-    dt = time.perf_counter() - t0
-    return {"value": FLOP_PER_SITE * vh / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"one oracle parity Dslash (hop_block, numpy FP64) on 32^3x64, {dt:.1f} s"}
+    pq = solve.vdot(p, q).real
+    x = x + (1.0 / pq) * p
+    r = r - (1.0 / pq) * q
+    rho = solve.norm2(r)
+    p = r + (rho / pq) * p
+    return time.perf_counter() - t0
 
 
-def make_inputs(device):
-    import torch
+def oracle_cpu_study(fields, fp64_iters, full=False, pool_procs=None):
+    """Oracle timings on this host.
 
+    fields: lattice key -> (u, psi) canonical numpy arrays (may be memory
+    mapped); fp64_iters: config name -> iterations of the plain FP64 GPU solve
+    of that workload (for the labelled extrapolations).  full: also run the
+    whole oracle solve of the 16^3x32 workload (minutes on one core).
+    """
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import oracle
+
+    info = host_cpu_info()
+    nproc = pool_procs or info["nproc"]
+    _CPU_FIELDS.clear()
+    _CPU_FIELDS.update(fields)
+    apply1, applyn, vec = {}, {}, {}
+    pool = mp.get_context("fork").Pool(nproc)
+    try:
+        for key, (u, psi) in fields.items():
+            dims = tuple(int(v) for v in key.split("x"))
+            sites = _parity_sites(dims)
+            tasks = [(key, c) for c in np.array_split(sites, nproc)]
+            pool.map(_cpu_hop_chunk, tasks)  # pages the inputs in
+            t0 = time.perf_counter()
+            oracle.hop_sites(u, psi, BC, sites)
+            apply1[key] = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pool.map(_cpu_hop_chunk, tasks)
+            applyn[key] = time.perf_counter() - t0
+            vec[key] = _cpu_vector_ops_s(dims)
+    finally:
+        pool.close()
+        pool.join()
+    out = {}
+    for name, lats, eps, kappa, cfg, nrhs in CPU_CONFIGS:
+        keys = [_lat_key(d) for d in lats]
+        if not all(k in fields for k in keys):
+            continue
+        vh = sum(int(np.prod(d)) // 2 for d in lats)
+        a1 = nrhs * sum(apply1[k] for k in keys)
+        an = nrhs * sum(applyn[k] for k in keys)
+        vv = nrhs * sum(vec[k] for k in keys)
+        row = {"sites_per_parity": vh, "rhs": nrhs,
+               "apply_s_1core": a1, "apply_s_allcore": an,
+               "gflops_1core": FLOP_PER_SITE * vh * nrhs / a1 / 1e9,
+               "gflops_allcore": FLOP_PER_SITE * vh * nrhs / an / 1e9,
+               "iter_s_1core": 4 * a1 + vv, "iter_s_allcore": 4 * an + vv,
+               "iter_kind": "derived: 4 parity applies (hop_sites) + the CG's vector operations timed on one core"}
+        iters = fp64_iters.get(name)
+        if iters:
+            row["fp64_iters_gpu"] = iters
+            row["solve_s_1core_extrapolated"] = iters * row["iter_s_1core"]
+            row["solve_s_allcore_extrapolated"] = iters * row["iter_s_allcore"]
+        out[name] = row
+    # whole oracle solves (the oracle's own cg, one core)
+    if "4x4x4x4" in fields:
+        u, b = fields["4x4x4x4"]
+        t0 = time.perf_counter()
+        _, it, res = oracle.solve_normal_full(np.asarray(u), np.asarray(b), 0.12, BC, tol=TOL)
+        dt = time.perf_counter() - t0
+        out["4x4x4x4"].update({"solve_s_1core_measured": dt, "solve_iters": it, "solve_true_rel_resid": res,
+                               "solve_kind": "oracle.solve_normal_full (CG on D^dag D), one core"})
+    if full and "16x16x16x32" in fields:
+        u, b = fields["16x16x16x32"]
+        t0 = time.perf_counter()
+        _, it, res = oracle.solve_normal_eo(np.asarray(u), np.asarray(b), 0.125, BC, tol=TOL)
+        dt = time.perf_counter() - t0
+        out["16x16x16x32"].update({"solve_s_1core_measured": dt, "solve_iters": it, "solve_true_rel_resid": res,
+                                   "iter_s_1core_measured": dt / max(it, 1),
+                                   "solve_kind": "oracle.solve_normal_eo (CG on Mhat^dag Mhat), one core"})
+    info.update({"pool_processes": nproc, "configs": out})
+    return info
+
+
+def cpu_study_inputs(device):
+    """Inputs of the CPU study on `device` (numpy on the host): lattice key ->
+    (links, source), the links and sources of each workload."""
     import synth
 
-    u = synth.gauge_field(DIMS, EPS, synth.seed_for(CONFIG_ID, 0), device=device, as_numpy=False)
-    b = torch.from_numpy(synth.gaussian_spinor(DIMS, synth.seed_for(CONFIG_ID, 1))).to(device)
-    return u, b
+    fields = {}
+    for name, lats, eps, kappa, cfg, nrhs in CPU_CONFIGS:
+        for k, d in enumerate(lats):
+            key = _lat_key(d)
+            if key in fields:
+                continue
+            seed_u = synth.seed_for(cfg, 0) if len(lats) == 1 else synth.seed_for(cfg, 4 + k)
+            u = synth.gauge_field_device(d, eps, seed_u, device=device).cpu().numpy()
+            b = synth.gaussian_spinor_device(d, synth.seed_for(cfg, 1), device=device).cpu().numpy()
+            fields[key] = (u, b)
+    return fields
+
+
+def config1_fp64_iters(cola, dev):
+    """Iterations of the plain FP64 even-odd GPU solve of the 16^3x32 workload."""
+    import synth
+
+    d = (16, 16, 16, 32)
+    u = synth.gauge_field_device(d, 0.3, synth.seed_for(1, 0), device=dev)
+    b = synth.gaussian_spinor_device(d, synth.seed_for(1, 1), device=dev)
+    g = cola.Gauge(u, d, 0.125, BC, precisions=("f64",), recon={"f64": 12})
+    _, info = cola.cg_solve(g, b, tol=TOL, op="eo", inner="f64", use_graph=True)
+    return info[0].iters
+
+
+def run_cpu_study_child(args):
+    """--cpu-study DIR: the oracle timings on inputs saved under DIR (a
+    process without CUDA), one JSON line on stdout."""
+    import numpy as np
+
+    spec = json.load(open(os.path.join(args.cpu_study, "spec.json")))
+    fields = {}
+    for key in spec["lattices"]:
+        fields[key] = (np.load(os.path.join(args.cpu_study, f"u_{key}.npy")),
+                       np.load(os.path.join(args.cpu_study, f"b_{key}.npy")))
+    print(json.dumps(oracle_cpu_study(fields, spec["fp64_iters"], full=args.cpu_full)), flush=True)
+
+
+def cpu_baseline_from_study(study):
+    """The bench line's cpu_baseline object: the headline workload's parity
+    apply on every core, with the whole study beside it."""
+    head = study["configs"]["32x32x32x64"]
+    return {"value": head["gflops_allcore"], "unit": "GFLOP/s", "cores": study["pool_processes"], "kind": "oracle",
+            "sample": "one oracle parity Dslash (hop_sites, numpy FP64) over the 1,048,576 even sites of 32^3x64, "
+                      f"in {study['pool_processes']} site chunks on as many processes; per-config table beside it",
+            "cpu_model": study["cpu_model"], "nproc": study["nproc"],
+            "one_core_gflops": head["gflops_1core"], "configs": study["configs"]}
+
+
+def run_cpu_study_from_gpu_arm(cola_iters, full=False):
+    """Save the study's inputs (drawn on the GPU) and time the oracle in a child process."""
+    import shutil
+
+    import numpy as np
+    import torch
+
+    d = tempfile.mkdtemp(prefix="cola_cpu_study_")
+    try:
+        fields = cpu_study_inputs(torch.device("cuda", torch.cuda.current_device()))
+        for key, (u, b) in fields.items():
+            np.save(os.path.join(d, f"u_{key}.npy"), u)
+            np.save(os.path.join(d, f"b_{key}.npy"), b)
+        del fields
+        with open(os.path.join(d, "spec.json"), "w") as f:
+            json.dump({"lattices": [_lat_key(l) for _, lats, *_ in CPU_CONFIGS for l in lats],
+                       "fp64_iters": cola_iters}, f)
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-study", d] + (["--cpu-full"] if full else [])
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=3600)
+        if r.returncode != 0:
+            return {"error": f"cpu study exited {r.returncode}: {r.stderr[-400:]}"}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
 
 
 def run_reference(args):
+    """--impl reference: the oracle on the host cores, on the bench's workload.
+
+    Each step is a bounded sample of the same workload: one parity Dslash of
+    the 32^3x64 eo solve (the operator the solve applies four times per
+    iteration), by the oracle's hop_sites over disjoint site chunks on every
+    host core.  No GPU is used: the inputs are drawn by the seeded generator
+    with torch on the CPU.
+    """
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
+    import multiprocessing as mp
+
+    import numpy as np
 
     import oracle
     import synth
 
-    u = synth.gauge_field(DIMS, EPS, synth.seed_for(CONFIG_ID, 0))
-    psi = synth.gaussian_spinor(DIMS, synth.seed_for(CONFIG_ID, 1))
-    vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
-    for _ in range(args.warmup):
-        oracle.hop_block(u, psi, BC, 0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.hop_block(u, psi, BC, 0)
-    dt = time.perf_counter() - t0
+    u = synth.gauge_field_device(DIMS, EPS, synth.seed_for(CONFIG_ID, 0), device="cpu").numpy()
+    psi = synth.gaussian_spinor_device(DIMS, synth.seed_for(CONFIG_ID, 1), device="cpu").numpy()
+    key = _lat_key(DIMS)
+    _CPU_FIELDS.clear()
+    _CPU_FIELDS[key] = (u, psi)
+    info = host_cpu_info()
+    nproc = info["nproc"]
+    sites = _parity_sites(DIMS)
+    vh = len(sites)
+    tasks = [(key, c) for c in np.array_split(sites, nproc)]
+    pool = mp.get_context("fork").Pool(nproc)
+    try:
+        for _ in range(args.warmup):
+            pool.map(_cpu_hop_chunk, tasks)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_cpu_hop_chunk, tasks)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
     value = FLOP_PER_SITE * vh * args.steps / dt / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA,
-                   "step": "one oracle parity Dslash apply (numpy FP64, CPU)"},
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle parity Dslash applies on 32^3x64"},
+        "config": bench_config(world),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": nproc, "kind": "oracle",
+                         "sample": f"each step one oracle parity Dslash (hop_sites, numpy FP64) over the {vh} even "
+                                   f"sites of 32^3x64 in {nproc} site chunks on as many processes",
+                         "cpu_model": info["cpu_model"], "nproc": info["nproc"]},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def bench_config(world):
+    return {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA, "links": "exp(0.25 i H)",
+            "inner": "f16 (per-site scale), 12-real links", "delta": DELTA, "tol": TOL,
+            "l2": "inputs larger than L2 (FP16 links 201 MB, FP64 source 403 MB)",
+            "parallelism": f"replicas{world}"}
 
 
 def run_cola(args):
@@ -292,6 +589,8 @@ def run_cola(args):
     d1.record(stream)
     torch.cuda.synchronize()
     ds64_us = d0.elapsed_time(d1) * 1e3 / 20
+    fp64_peak = measure_fp64_peak(cola, dev, stream)
+    FP64_PEAK_MEASURED[0] = fp64_peak
 
     # isolated FP32 parity Dslash (the FP32-storage solver's kernel), own handle
     g32 = cola.Gauge(u, DIMS, KAPPA, BC, precisions=("f32",), recon={"f32": 12})
@@ -336,7 +635,7 @@ def run_cola(args):
     # region.
     u_host = u.cpu().pin_memory()
     b_host = b.cpu().pin_memory()
-    e2e_steps = max(2, min(args.steps, 4))
+    e2e_steps = max(2, args.steps)
     x_host = [torch.empty_like(b_host).pin_memory() for _ in range(2)]
     ud = [torch.empty_like(u) for _ in range(2)]
     bd = [torch.empty_like(b) for _ in range(2)]
@@ -375,17 +674,20 @@ def run_cola(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(u.cpu().numpy(), b.cpu().numpy())
+        # iterations of the plain FP64 GPU solves, for the oracle study's
+        # labelled whole-solve extrapolations
+        fp64_iters = {"32x32x32x64": info64[0].iters, "16x16x16x32": config1_fp64_iters(cola, dev)}
+        if multi and "point_sources_24x24x24x48" in multi:
+            fp64_iters["24x24x24x48-12-point-sources"] = multi["point_sources_24x24x24x48"]["fp64_iters"]
+        study = run_cpu_study_from_gpu_arm(fp64_iters, full=args.cpu_full)
+        cpu = study if "error" in study else cpu_baseline_from_study(study)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mixed_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f16-storage/f32-math/f64-reliable", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA, "links": "exp(0.25 i H)",
-                       "inner": "f16 (per-site scale), 12-real links", "delta": DELTA, "tol": TOL,
-                       "l2": "inputs larger than L2 (FP16 links 201 MB, FP64 source 403 MB)",
-                       "parallelism": f"replicas{world}"},
+            "config": bench_config(world),
             "solve": {"iters": iters[-1], "reliable_updates": rus[-1],
                       "true_rel_resid": infos[-1].true_rel_resid, "mixed_ms": mixed_ms},
             "fp64_cg": {"ms": fp64_ms, "iters": info64[0].iters, "true_rel_resid": info64[0].true_rel_resid,
@@ -398,14 +700,16 @@ def run_cola(args):
             # dominant kernel by time share: the FP64 hopping term of the reliable
             # updates (about half of the solve), bound by the FP64 pipe
             "roofline": {"bound": "alu", "achieved": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,
-                         "traffic": NCU_TRAFFIC["f64"], "kernel": "dslash_kernel<F64,18> parity apply",
-                         "peak_kind": "FP64 peak derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2 "
-                                      "flop x 2.07 GHz); 1320 algorithmic flop per site"},
+                         "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12 / fp64_peak,
+                         "traffic": ncu_traffic("f64"), "kernel": "dslash_kernel<F64,18> parity apply",
+                         "peak_kind": "measured in this run: independent FP64 FMA chains (cola_probe_fp64_fma), "
+                                      "CUDA events, best of 5; 1320 algorithmic flop per site",
+                         "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
+                         "frac_of_derived": FLOP_PER_SITE * vh / (ds64_us * 1e-6) / 1e12 / FP64_PEAK_DERIVED_TFLOPS},
             # the inner-iteration kernel, bound by HBM
             "roofline_inner": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                               "frac": achieved / peak, "traffic": NCU_TRAFFIC["f16"],
+                               "frac": achieved / peak, "traffic": ncu_traffic("f16"),
                                "kernel": "dslash_kernel<F16,12> parity apply",
                                "peak_kind": f"{peak_kind} hbm_gbs (burst, kernel timed alone)"},
             "e2e": {"value": e2e_value, "unit": "GFLOP/s",
@@ -648,10 +952,10 @@ def hmc_measurements(cola, dev):
         "trajectory_s": info.seconds, "force_evals": info.force_evals, "cg_iters": info.cg_iters, "dH": info.dH,
         "accepted": info.accepted, "plaquette": info.plaquette,
         "variants_s": {f"{k[0]}/{k[1]}": v.seconds for k, v in variants.items()},
-        "gauge_force_us": gf_us, "gauge_force_fp64_tflops": gf_tflops, "gauge_force_frac_fp64": gf_tflops / FP64_PEAK_TFLOPS,
+        "gauge_force_us": gf_us, "gauge_force_fp64_tflops": gf_tflops, "gauge_force_frac_fp64": gf_tflops / FP64_PEAK_MEASURED[0],
         "link_update_and_repack_us": lu_us,
         "fermion_force_us": ff_us, "clover_force_us": cf_us, "clover_force_fp64_tflops": cf_tflops,
-        "clover_force_frac_fp64": cf_tflops / FP64_PEAK_TFLOPS,
+        "clover_force_frac_fp64": cf_tflops / FP64_PEAK_MEASURED[0],
         "clover_trajectory": {"csw": 1.0, "trajectory_s": info_c.seconds, "cg_iters": info_c.cg_iters,
                               "dH": info_c.dH, "accepted": info_c.accepted},
     }
@@ -832,6 +1136,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cola", choices=["cola", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="the oracle study also runs the whole 16^3x32 oracle solve (minutes on one core)")
+    ap.add_argument("--cpu-study", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-study-only", action="store_true",
+                    help="run only the oracle study on the host cores (inputs drawn on the GPU) and print it")
     ap.add_argument("--skip-multi-rhs", action="store_true", help="skip the multi-RHS and batched solves")
     ap.add_argument("--skip-clover", action="store_true", help="skip the clover-operator measurements")
     ap.add_argument("--skip-hmc", action="store_true", help="skip the HMC trajectory measurement")
@@ -843,7 +1152,14 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
-    if args.dslash_only:
+    if args.cpu_study:
+        run_cpu_study_child(args)
+    elif args.cpu_study_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps(run_cpu_study_from_gpu_arm({}, full=args.cpu_full)), flush=True)
+    elif args.dslash_only:
         run_dslash_only(args)
     elif args.gauge_only:
         run_gauge_only(args)

@@ -143,9 +143,15 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
  * of this library.  It calls no allocator; its temporaries live in one
  * static device array of 64 MiB that the library holds on each device until
  * the process exits.  A call needs cola_spinor_bytes(lat, prec, nrhs) bytes
- * of that array and returns COLA_ERR_ARG above 64 MiB.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * of that array and returns COLA_ERR_ARG above 64 MiB.  Every call looks up
+ * the array's device address in the current device's context
+ * (cudaGetSymbolAddress), so a context that was reset and created again gets
+ * the new address; the first call in a context may load the library's device
+ * code there, so make that first call before any stream capture.  With
+ * lazy module loading (the CUDA default) the array is reserved on a device
+ * when this part of the library is first used there; with
+ * CUDA_MODULE_LOADING=EAGER every process that loads the library reserves it
+ * on each device it uses, even if it never calls this entry point.
  * All calls share the array: calls whose work overlaps on the GPU (other
  * streams, unordered threads) race, so order them. */
 cola_status cola_mdagm_apply_noalloc(cola_gauge g, void *out, const void *in, int op, cola_prec prec,
@@ -378,6 +384,19 @@ cola_status cola_hmc_trajectory(cola_gauge g, void *links_dev, double *mom_dev, 
 
 /* Thread-local message describing the last error returned on this thread. */
 const char *cola_last_error(void);
+
+/* Measurement aid with no counterpart in the paper: launches on `stream`
+ * one kernel of `blocks` x `threads` threads, each running 8 independent
+ * FP64 fused multiply-add chains for `steps` steps, and returns in *flop
+ * (host) the floating-point operations that launch performs
+ * (2 x 8 x steps x threads x blocks).  Timing the launch with events on the
+ * same stream gives the FP64 arithmetic rate the FP64 hopping term is bound
+ * by.  out (device) receives blocks x threads doubles (the chains' sums), so
+ * that no work is optimised away.  Returns COLA_ERR_ARG unless threads is a
+ * multiple of 32 in 32..256, blocks in 1..2^20 and steps a positive
+ * multiple of 4.  Does not wait for the device. */
+cola_status cola_probe_fp64_fma(double *out, int blocks, int threads, int steps, cudaStream_t stream,
+                                double *flop);
 
 /* Debug builds only (libcola compiled with -DCOLA_BOUNDS): every neighbour,
  * link and site index the kernels compute is checked against its extent; an

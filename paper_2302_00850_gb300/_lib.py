@@ -109,6 +109,7 @@ SIGNATURES = {
     "cola_hmc_trajectory": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(HmcParams), ctypes.POINTER(HmcInfo), _vp]),
     "cola_last_error": (ctypes.c_char_p, []),
     "cola_debug_bounds": (_st, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(_i), _i]),
+    "cola_probe_fp64_fma": (_st, [_vp, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None

@@ -392,3 +392,15 @@ def debug_bounds(reset: bool = False) -> tuple[int, int]:
     count, line = ctypes.c_ulonglong(0), ctypes.c_int(0)
     check(lib.cola_debug_bounds(ctypes.byref(count), ctypes.byref(line), int(bool(reset))))
     return int(count.value), int(line.value)
+
+
+def probe_fp64_fma(out: torch.Tensor, blocks: int, threads: int = 256, steps: int = 4096) -> float:
+    """Launch the FP64 fused-multiply-add probe on the current stream (no wait);
+    returns the flop count of the launch.  out: float64 on the device with at
+    least blocks * threads elements."""
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < blocks * threads:
+        raise ValueError("out must be a CUDA float64 tensor of at least blocks * threads elements")
+    flop = ctypes.c_double(0.0)
+    check(_lib.load().cola_probe_fp64_fma(_ptr(out), int(blocks), int(threads), int(steps), _stream(out.device),
+                                          ctypes.byref(flop)))
+    return float(flop.value)

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcola.so")
 SOURCES = ["dslash.cu", "dslash_clover.cu", "clover.cu", "clover_force.cu", "blas.cu", "pack.cu", "force.cu", "gauge.cu", "hmc.cu",
-           "solver.cu", "multishift.cu", "eig.cu", "api.cu", "noalloc.cu"]
+           "solver.cu", "multishift.cu", "eig.cu", "api.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -104,9 +104,15 @@ static thread_local int g_tune_only = 0;
 TuneOnlyScope::TuneOnlyScope() { ++g_tune_only; }
 TuneOnlyScope::~TuneOnlyScope() { --g_tune_only; }
 
-static bool outputs_alias_inputs(const DslashArgs &A) {
-    for (int l = 0; l < A.nlat; ++l)
-        if (A.lat[l].out == A.lat[l].in || A.lat[l].out == A.lat[l].xin) return true;
+// True if the launch's tuning runs could change an input.  A single-parity
+// launch writes only parity p of out and reads parity 1 - p of in, so out ==
+// in (one field holding two temporaries in its two parity halves) is no
+// alias there; the xpay input is read at parity p and always is one.
+static bool outputs_alias_inputs(const DslashArgs &A, int nparity) {
+    for (int l = 0; l < A.nlat; ++l) {
+        if (A.lat[l].out == A.lat[l].xin) return true;
+        if (A.lat[l].out == A.lat[l].in && nparity != 1) return true;
+    }
     return false;
 }
 
@@ -162,7 +168,7 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
             if (it == g_tune.end()) {
                 cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
                 if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
-                    !outputs_alias_inputs(A)) {
+                    !outputs_alias_inputs(A, nparity)) {
                     tune_store_locked(key, tune(prec, recon, A, nparity, dagger, epi, s));
                     it = g_tune.find(key);
                 }

@@ -10,7 +10,10 @@
 // temporaries in the gauge handle on first use; this variant instead uses
 // one file-scope device array of fixed size, kStaticScratchBytes (64 MiB),
 // that lives in the library's device image.  A GPU that has loaded this part
-// of the library keeps that array until the process exits.
+// of the library keeps that array until the process exits.  With lazy module
+// loading (the CUDA default) that happens at the first call on the device;
+// with CUDA_MODULE_LOADING=EAGER every process that loads libcola reserves it
+// on every device it uses, whether or not it ever calls this entry point.
 //
 // The scratch holds one packed spinor field per right-hand side in the
 // requested precision: the even-odd operator puts its odd-parity temporary
@@ -24,39 +27,27 @@
 // temporary is written in full before it is read, so nothing has to start at
 // zero; but calls whose work overlaps on the GPU (on different streams, or
 // from several threads without ordering) race on the array.
-#include <mutex>
-
 #include "cola_impl.h"
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch per device.  In host code the symbol
-// name is only a host-side handle, so the address is looked up once per
-// device, with that device current, on the first call made on it.
-void *g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
+// Device address of g_static_scratch in the current device's context.  In
+// host code the symbol name is only a host-side handle, never a device
+// address.  The lookup is repeated on every call rather than cached: after a
+// cudaDeviceReset, or when the primary context is released and created again,
+// the library's device code is loaded anew and the array can sit at another
+// address, so a cached pointer would be stale.  Once the device code is
+// loaded in the current context the lookup is a host-side table query; the
+// first call in a context may load that code.
 cola_status static_scratch(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cola::cuda_check(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        cola::set_error("device ordinal above the static-scratch table size");
-        return COLA_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cola::cuda_check(e, "cudaGetSymbolAddress(static scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cola::cuda_check(e, "cudaGetSymbolAddress(static scratch)");
+    *out = p;
     return COLA_OK;
 }
 

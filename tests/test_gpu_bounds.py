@@ -106,5 +106,5 @@ def test_bounds_build_reports_no_violation():
         elif k.startswith("dirac"):
             assert v < (1e-6 if k.endswith("f32") else 2e-3), (k, v)
         elif k.startswith(("solve", "multishift", "batched")):
-            assert v <= 1.05e-10, (k, v)
+            assert v <= 1e-10, (k, v)
     assert res["hmc dH"] == res["hmc dH"], res  # a number, not NaN

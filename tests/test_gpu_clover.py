@@ -156,7 +156,7 @@ def test_clover_eo_normal_solve(cola, inner, use_graph):
     g = clover_gauge(cola, u, dims)
     x, info = cola.cg_solve(g, to_dev(b), tol=1e-10, op="eo", inner=inner, use_graph=use_graph)
     assert info[0].status == 0
-    assert resid_eo(u, x.cpu().numpy(), b, dims) <= 1.05e-10
+    assert resid_eo(u, x.cpu().numpy(), b, dims) <= 1e-10
     if inner != "f64":
         assert info[0].reliable_updates >= 2
 
@@ -187,7 +187,7 @@ def test_clover_multi_rhs_matches_single(cola):
     x = x.cpu().numpy()
     for r in range(3):
         assert info[r].status == 0
-        assert resid_eo(u, x[r], b[r], dims) <= 1.05e-10
+        assert resid_eo(u, x[r], b[r], dims) <= 1e-10
         x1, _ = cola.cg_solve(g, to_dev(b[r]), tol=1e-10, op="eo", inner="f32", use_graph=True)
         assert rel_err(x[r], x1.cpu().numpy()) < 1e-8
 
@@ -277,11 +277,11 @@ def test_multishift_and_eigensolver_on_a_clover_handle(cola):
     for k, sg in enumerate(shifts):
         xk = x[k].cpu().numpy() * e
         assert infos[k].status == 0
-        assert rel_err(op(xk) + sg * xk, b * e) <= 1.05e-10
+        assert rel_err(op(xk) + sg * xk, b * e) <= 1e-10
     v0 = to_dev(synth.gaussian_spinor(dims, synth.seed_for(74, 3), nrhs=6))
     vals, vecs, info = cola.eig_lowest(g, v0, nev=4, op="eo", tol=1e-9)
     want, _ = oeig.lowest_dense(op, dims[::-1] + (4, 3), 4, mask=e)
     assert info.status == 0
     assert np.max(np.abs(vals.numpy() - want) / want) < 1e-9
     res = oeig.residuals(op, vals.numpy(), vecs.cpu().numpy())
-    assert np.all(res <= 1.05e-9 * vals.numpy())
+    assert np.all(res <= 1e-9 * vals.numpy())

@@ -50,7 +50,7 @@ def check_vectors(apply_a, vals, vecs, mask, tol):
     gram = flat.conj() @ flat.T
     assert np.max(np.abs(gram - np.eye(n))) < 1e-12
     res = oeig.residuals(apply_a, vals, vecs)
-    assert np.all(res <= 1.05 * tol * np.abs(vals)), res / vals
+    assert np.all(res <= tol * np.abs(vals)), res / vals
     if mask is not None:
         assert np.max(np.abs(vecs * (1 - mask))) == 0.0
 

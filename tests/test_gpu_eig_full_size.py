@@ -51,4 +51,4 @@ def test_lowest_twelve_16x16x16x32(cola):
         rq = np.vdot(vecs[j].reshape(-1), av.reshape(-1)).real
         assert abs(rq - vals[j]) < 1e-10 * vals[j]
         res = oeig.residuals(op, [vals[j]], [vecs[j]])[0]
-        assert res <= 1.05e-8 * vals[j], res / vals[j]
+        assert res <= 1e-8 * vals[j], res / vals[j]

@@ -47,7 +47,7 @@ def check_against_oracle(u, b, dims, op, shifts, x, infos, tol, sol_tol):
         xi = x[i] * mask
         res = rel_err(apply_a(xi) + sigma * xi, bm)
         assert infos[i].status == 0, (i, sigma)
-        assert res <= 1.05 * tol, (i, sigma, res)
+        assert res <= tol, (i, sigma, res)
         assert abs(infos[i].true_rel_resid - res) < 1e-12
         assert rel_err(xi, xo[i]) < sol_tol, (i, sigma)
         if op == "eo":

@@ -173,3 +173,13 @@ def test_solver_parameter_errors_before_any_cuda_call(lib):
     prm = _lib.SolverParams(1e-10, 10, 1, 0, 0, 0.1, 1, 0)
     assert lib.cola_cg_solve_batched(0, hs, hs, hs, ctypes.byref(prm), info, None) == -1
     assert lib.cola_cg_solve_batched(9, hs, hs, hs, ctypes.byref(prm), info, None) == -1
+
+
+def test_fp64_probe_parameter_errors_before_any_cuda_call(lib):
+    fake = ctypes.c_void_p(1)  # never dereferenced: parameters are checked first
+    flop = ctypes.c_double(0.0)
+    for blocks, threads, steps in [(0, 256, 4096), (1216, 33, 4096), (1216, 512, 4096), (1216, 256, 4098),
+                                   (1216, 256, 0)]:
+        assert lib.cola_probe_fp64_fma(fake, blocks, threads, steps, None, ctypes.byref(flop)) == -1
+    assert lib.cola_probe_fp64_fma(None, 1216, 256, 4096, None, ctypes.byref(flop)) == -1
+    assert lib.cola_probe_fp64_fma(fake, 1216, 256, 4096, None, None) == -1

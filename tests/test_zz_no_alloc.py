@@ -67,6 +67,43 @@ def test_noalloc_matches_mdagm_on_two_calls(cola):
             assert rel_err(a * e, oracle.mdagm_eo(u, psi * e, kappa, BC_AP)) < 1e-13
 
 
+def test_noalloc_with_clover_term_allocates_nothing(cola):
+    """On a handle with a clover term the entry point applies the clover
+    operator (A_ee - kappa^2 H_eo A_oo^-1 H_oe on the even half), matches
+    cola_mdagm_apply and the oracle, and the device's free memory is the same
+    before and after two calls in a row (nothing was allocated)."""
+    import torch
+
+    import oracle.clover as ocl
+
+    dims = (4, 6, 4, 8)
+    kappa, csw = 0.124, 1.2
+    u = synth.gauge_field(dims, 0.3, synth.seed_for(61, 0))
+    g = cola.Gauge(to_dev(u), dims, kappa, BC_AP, precisions=("f64",))
+    g.attach_clover(csw)
+    e = oracle.even_mask(dims)[..., None, None]
+    outs = []
+    for k in range(2):
+        psi = synth.gaussian_spinor(dims, synth.seed_for(61, 1 + k))
+        pin = cola.pack(g, to_dev(psi), "f64")
+        ref = torch.zeros_like(pin)
+        got = torch.zeros_like(pin)
+        cola.mdagm(g, ref, pin, op="eo", prec="f64")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        assert _noalloc(cola, g, got, pin, "eo", "f64") == 0
+        assert _noalloc(cola, g, got, pin, "eo", "f64") == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        a = cola.unpack(g, got, "f64").cpu().numpy()
+        b = cola.unpack(g, ref, "f64").cpu().numpy()
+        assert rel_err(a * e, b * e) <= TOL["f64"]
+        want = ocl.mdagm_eo_clover(u, psi * e, kappa, BC_AP, csw)
+        assert rel_err(a * e, want * e) < 1e-13
+        outs.append(a)
+    assert rel_err(outs[0], outs[1]) > 0.1  # the two inputs differ, so must the outputs
+
+
 def test_noalloc_rejects_sizes_above_its_static_scratch(cola):
     dims = (16, 16, 16, 32)
     u = synth.unit_gauge(dims)
