@@ -479,6 +479,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def make_inputs(device):
+    import torch
+
+    import synth
+
+    u = synth.gauge_field(DIMS, EPS, synth.seed_for(CONFIG_ID, 0), device=device, as_numpy=False)
+    b = torch.from_numpy(synth.gaussian_spinor(DIMS, synth.seed_for(CONFIG_ID, 1))).to(device)
+    return u, b
+
+
 def bench_config(world):
     return {"workload": WORKLOAD, "lattice": "32x32x32x64", "kappa": KAPPA, "links": "exp(0.25 i H)",
             "inner": "f16 (per-site scale), 12-real links", "delta": DELTA, "tol": TOL,
@@ -763,11 +773,43 @@ def multi_rhs_measurements(cola, dev):
     ms12, (x12, i12) = timed(lambda: cola.cg_solve(g24, pts, tol=TOL, op="eo", inner="f32", delta=DELTA,
                                                    use_graph=True))
     ms64, (x64, i64) = timed(lambda: cola.cg_solve(g24, pts[0], tol=TOL, op="eo", inner="f64", use_graph=True))
+    # the same 12 sources as 12 single-right-hand-side solves of the same kind
+    cola.cg_solve(g24, pts[0], tol=TOL, op="eo", inner="f32", delta=DELTA, use_graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    singles = [cola.cg_solve(g24, pts[k], tol=TOL, op="eo", inner="f32", delta=DELTA, use_graph=True)[1][0]
+               for k in range(12)]
+    e1.record()
+    torch.cuda.synchronize()
+    ms1x12 = e0.elapsed_time(e1)
+    # the FP32 parity hopping term alone: 12 right-hand sides in one launch against one
+    def hop_us(nrhs, reps=20):
+        pin = cola.pack(g24, pts[:nrhs] if nrhs > 1 else pts[0], "f32")
+        pout = g24.empty_packed("f32", nrhs)
+        cola.dslash(g24, pout, pin, parity=1, prec="f32", nrhs=nrhs)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record()
+        for _ in range(reps):
+            cola.dslash(g24, pout, pin, parity=1, prec="f32", nrhs=nrhs)
+        h1.record()
+        torch.cuda.synchronize()
+        return h0.elapsed_time(h1) * 1e3 / reps
+    us1, us12 = hop_us(1), hop_us(12)
+    vh24 = 24 ** 3 * 48 // 2
     out["point_sources_24x24x24x48"] = {
         "nrhs": 12, "mixed_f32_ms": ms12, "mixed_ms_per_rhs": ms12 / 12,
         "max_iters": max(i.iters for i in i12), "max_true_rel_resid": max(i.true_rel_resid for i in i12),
+        "single_rhs_f32_solves_ms": ms1x12, "single_rhs_f32_ms_per_rhs": ms1x12 / 12,
+        "single_rhs_max_true_rel_resid": max(i.true_rel_resid for i in singles),
+        "per_rhs_ratio_vs_single_rhs_f32": ms12 / ms1x12,
         "fp64_single_rhs_ms": ms64, "fp64_iters": i64[0].iters,
-        "per_rhs_ratio_vs_fp64": (ms12 / 12) / ms64}
+        "per_rhs_ratio_vs_fp64": (ms12 / 12) / ms64,
+        "dslash_f32_us_1rhs": us1, "dslash_f32_us_per_rhs_12rhs": us12 / 12,
+        # algorithmic bytes per output site and right-hand side: spinor in and out
+        # (2 x 96 B) plus the 8 links (8 x 48 B) shared by the right-hand sides of a launch
+        "dslash_f32_12rhs_algorithmic_gbs": (12 * 192 + 384) * vh24 / (us12 * 1e-6) / 1e9}
     dims_list = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), d24]
     gauges, bs = [], []
     for k, d in enumerate(dims_list):

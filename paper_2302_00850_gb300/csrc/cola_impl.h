@@ -35,7 +35,8 @@ struct DslashLat {
 struct DslashArgs {
     int nlat;
     int nrhs;
-    int rhs_per_block;
+    int rhs_per_block;            // threads per block along right-hand sides (blockDim.y)
+    int rhs_per_thread;           // right-hand sides each thread carries (0 or 1: one)
     int parity0;                  // first output parity (blockIdx.z adds 0 or 1)
     DslashLat lat[kMaxBatch];
     CgState *state;               // solver mode: skip finished rows

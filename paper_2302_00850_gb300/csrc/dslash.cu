@@ -27,7 +27,11 @@ static int assign_blocks(DslashArgs &A, int bx) {
 
 static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, bool dagger, int epi, int block_x,
                               cudaStream_t s) {
-    A.ngroups = (A.nrhs + A.rhs_per_block - 1) / A.rhs_per_block;
+    if (A.rhs_per_thread < 1) A.rhs_per_thread = 1;
+    if (!mrhs_supported(prec, A.rhs_per_thread) || (A.rhs_per_thread > 1 && staged_depth(prec) > 0))
+        return cudaErrorInvalidValue;
+    const int per_group = A.rhs_per_block * A.rhs_per_thread;
+    A.ngroups = (A.nrhs + per_group - 1) / per_group;
     const int nb = assign_blocks(A, block_x);
     if (epi == EPI_CLOVER_X || epi == EPI_CLOVER_INV)
         return launch_dslash_clover(prec, recon, A, nparity, dagger, epi, block_x, nb, s);
@@ -43,7 +47,7 @@ static cudaError_t launch_now(int prec, int recon, DslashArgs &A, int nparity, b
 // are kept per process and, with COLA_TUNE_CACHE=<file>, in that file.
 // COLA_TUNE=0 disables tuning (defaults are used).
 struct TuneEntry {
-    int bx, by;
+    int bx, by, nr;  // sites per block, right-hand sides per block (threads), right-hand sides per thread
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneEntry> g_tune;
@@ -72,10 +76,11 @@ static void tune_load_locked() {
     while (fgets(line, sizeof(line), f)) {
         char *bar = strrchr(line, '|');
         if (!bar) continue;
-        int bx = 0, by = 0;
-        if (sscanf(bar + 1, "%d %d", &bx, &by) != 2 || bx < 32 || by < 1) continue;
+        int bx = 0, by = 0, nr = 1;
+        const int n = sscanf(bar + 1, "%d %d %d", &bx, &by, &nr);
+        if (n < 2 || bx < 32 || by < 1 || nr < 1) continue;
         *bar = 0;
-        g_tune[std::string(line)] = {bx, by};
+        g_tune[std::string(line)] = {bx, by, n == 3 ? nr : 1};
     }
     fclose(f);
 }
@@ -86,7 +91,7 @@ static void tune_store_locked(const std::string &key, TuneEntry e) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s|%d %d\n", key.c_str(), e.bx, e.by);
+    fprintf(f, "%s|%d %d %d\n", key.c_str(), e.bx, e.by, e.nr);
     fclose(f);
 }
 
@@ -118,7 +123,7 @@ static bool outputs_alias_inputs(const DslashArgs &A, int nparity) {
 
 static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bool dagger, int epi,
                       cudaStream_t s) {
-    TuneEntry best = {default_dslash_block(prec, A0.rhs_per_block), A0.rhs_per_block};
+    TuneEntry best = {default_dslash_block(prec, A0.rhs_per_block), A0.rhs_per_block, 1};
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return best;
@@ -128,14 +133,18 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
     }
     const int bys[] = {1, 2, 4, 8};
     const int bxs[] = {32, 64, 128, 256};
+    const int nrs[] = {1, 2, 4};
     const bool staged = prec != COLA_F64 && staged_depth(prec) > 0;
+    for (int nr : nrs) {
+    if (!mrhs_supported(prec, nr) || (nr > 1 && staged) || nr > A0.nrhs) continue;
     for (int by : bys) {
-        if (by > A0.nrhs) continue;
+        if (by * nr > A0.nrhs && by > 1) continue;
         for (int bx : bxs) {
             if (bx * by > 256 || bx * by < 64) continue;
             if (staged && bx * by != kStagedThreads) continue;
             DslashArgs A = A0;
             A.rhs_per_block = by;
+            A.rhs_per_thread = nr;
             A.state = nullptr;
             A.filter_ru = 0;
             bool ok = launch_now(prec, recon, A, nparity, dagger, epi, bx, s) == cudaSuccess;
@@ -145,10 +154,11 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
             float ms = 0.f;
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
                 best_ms = ms;
-                best = {bx, by};
+                best = {bx, by, nr};
             }
             cudaGetLastError();
         }
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -176,6 +186,7 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
             if (it != g_tune.end()) {
                 block_x = it->second.bx;
                 A.rhs_per_block = it->second.by;
+                A.rhs_per_thread = it->second.nr;
             }
         }
     }

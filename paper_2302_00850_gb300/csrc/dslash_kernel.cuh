@@ -22,6 +22,8 @@
 // reconstruction, gamma matrices in the DeGrand-Rossi basis).
 #pragma once
 
+#include <type_traits>
+
 #include "cola_impl.h"
 
 #ifndef COLA_DSLASH_MINB
@@ -211,6 +213,15 @@ __device__ __forceinline__ void su3_adj_mul_add(const Cx<R> (&u)[9], const Cx<R>
 // w_f - w_b = 2 w_f - c: twelve multiply-adds fewer than two full
 // reconstructions.  Hops that cross the boundary (phase) or carry an FP16
 // site scale take the general form.
+template <int P, int MU, bool DAGGER>
+__device__ __forceinline__ void hop_pair_apply(const Geom &g, const Cx<typename Prec<P>::real> (&uf)[9],
+                                               const Cx<typename Prec<P>::real> (&ub)[9],
+                                               const Cx<typename Prec<P>::real> (&hf)[2][3],
+                                               const Cx<typename Prec<P>::real> (&hb)[2][3],
+                                               typename Prec<P>::real scf, typename Prec<P>::real scb, bool edge_f,
+                                               bool edge_b, Cx<typename Prec<P>::real> (&acc)[12],
+                                               typename Prec<P>::real bs);
+
 template <int P, int RECON, int MU, bool DAGGER>
 __device__ __forceinline__ void hop_mu(const DslashLat &A, const Coord &c, int cb, const char *in,
                                        const char *links_out, const char *links_in,
@@ -237,6 +248,64 @@ __device__ __forceinline__ void hop_mu(const DslashLat &A, const Coord &c, int c
     LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nbb, ub);
     const bool edge_f = !g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1;
     const bool edge_b = !g.bc_trivial[MU] && coord_of<MU>(c) == 0;
+    hop_pair_apply<P, MU, DAGGER>(g, uf, ub, hf, hb, scf, scb, edge_f, edge_b, acc, bs);
+}
+
+// Both hops of direction mu for NR right-hand sides of one site: each link is
+// loaded (and its third row rebuilt) once and applied to every right-hand
+// side, so link traffic and link arithmetic are shared by NR outputs.
+// in0 addresses right-hand side 0 of this thread; live[k] masks finished or
+// absent right-hand sides.
+template <int P, int RECON, int MU, bool DAGGER, int NR>
+__device__ __forceinline__ void hop_mu_mrhs(const DslashLat &A, const Coord &c, int cb, const char *in0,
+                                            const char *links_out, const char *links_in,
+                                            Cx<typename Prec<P>::real> (&acc)[NR][12], typename Prec<P>::real bs,
+                                            const bool (&live)[NR]) {
+    using R = typename Prec<P>::real;
+    const Geom &g = A.g;
+    constexpr int SF = DAGGER ? +1 : -1;
+    constexpr int SB = -SF;
+    const int nbf = nbr_cb<MU, +1>(g, c, cb);
+    const int nbb = nbr_cb<MU, -1>(g, c, cb);
+    Cx<R> uf[9], ub[9];
+    LinkIO<P, RECON>::load(links_out + MU * A.link_dir_stride, g.Vh, cb, uf);
+    LinkIO<P, RECON>::load(links_in + MU * A.link_dir_stride, g.Vh, nbb, ub);
+    const bool edge_f = !g.bc_trivial[MU] && coord_of<MU>(c) == g.L[MU] - 1;
+    const bool edge_b = !g.bc_trivial[MU] && coord_of<MU>(c) == 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        if (!live[k]) continue;
+        const char *in = in0 + (size_t)k * A.rhs_stride;
+        Cx<R> hf[2][3], hb[2][3];
+        R scf, scb;
+        {
+            Cx<R> psi[12];
+            scf = SpinorIO<P>::load_raw(in, g.Vh, nbf, psi);
+            project<MU, SF>(psi, hf);
+        }
+        {
+            Cx<R> psi[12];
+            scb = SpinorIO<P>::load_raw(in, g.Vh, nbb, psi);
+            project<MU, SB>(psi, hb);
+        }
+        hop_pair_apply<P, MU, DAGGER>(g, uf, ub, hf, hb, scf, scb, edge_f, edge_b, acc[k], bs);
+    }
+}
+
+// The forward hop (link uf, projected neighbour hf with site scale scf) and
+// the backward hop (ub, hb, scb) of direction mu, accumulated into acc with
+// the output factor bs.
+template <int P, int MU, bool DAGGER>
+__device__ __forceinline__ void hop_pair_apply(const Geom &g, const Cx<typename Prec<P>::real> (&uf)[9],
+                                               const Cx<typename Prec<P>::real> (&ub)[9],
+                                               const Cx<typename Prec<P>::real> (&hf)[2][3],
+                                               const Cx<typename Prec<P>::real> (&hb)[2][3],
+                                               typename Prec<P>::real scf, typename Prec<P>::real scb, bool edge_f,
+                                               bool edge_b, Cx<typename Prec<P>::real> (&acc)[12],
+                                               typename Prec<P>::real bs) {
+    using R = typename Prec<P>::real;
+    constexpr int SF = DAGGER ? +1 : -1;
+    constexpr int SB = -SF;
     Cx<R> wf[2][3];
     su3_mul(uf, hf, wf);
     if (P != COLA_F16 && !edge_f && !edge_b) {
@@ -354,42 +423,131 @@ __device__ __forceinline__ void stage_issue(const DslashLat &A, const Coord &c, 
     }
 }
 
+// FP16 spin projection straight from storage.  PTX for sm_100 and later
+// adds one FP16 operand to one FP32 operand with an FP32 result
+// (add/sub.rn.f32.f16); the FP16 value enters exactly, so a + b is rounded
+// once, exactly as converting a first and adding in FP32 would do, and one
+// conversion per component is saved.  A stored complex is a half2 word
+// (real part in the low half).
+__device__ __forceinline__ float hadd_lo(uint32_t a, float b) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.f16 %0, l, %2;}" : "=f"(r) : "r"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float hadd_hi(uint32_t a, float b) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n add.rn.f32.f16 %0, h, %2;}" : "=f"(r) : "r"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float hsub_lo(uint32_t a, float b) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n sub.rn.f32.f16 %0, l, %2;}" : "=f"(r) : "r"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float hsub_hi(uint32_t a, float b) {
+    float r;
+    asm("{.reg .b16 l, h;\n mov.b32 {l, h}, %1;\n sub.rn.f32.f16 %0, h, %2;}" : "=f"(r) : "r"(a), "f"(b));
+    return r;
+}
+// a + s b and a + s i b for a stored half2 complex a and an FP32 complex b
+template <int S>
+__device__ __forceinline__ Cx<float> hadd_s(uint32_t a, Cx<float> b) {
+    if constexpr (S > 0) return {hadd_lo(a, b.re), hadd_hi(a, b.im)};
+    else return {hsub_lo(a, b.re), hsub_hi(a, b.im)};
+}
+template <int S>
+__device__ __forceinline__ Cx<float> hadd_si(uint32_t a, Cx<float> b) {
+    if constexpr (S > 0) return {hsub_lo(a, b.im), hadd_hi(a, b.re)};
+    else return {hadd_lo(a, b.im), hsub_hi(a, b.re)};
+}
+__device__ __forceinline__ Cx<float> h2cx(uint32_t w) {
+    const float2 f = h2f(w);
+    return {f.x, f.y};
+}
+
+// Two-spinor h = rows 0, 1 of (1 + S gamma_mu) psi from a stored FP16 spinor
+// (unscaled; the site scale is applied with the hop's scale).  The same
+// combinations as project<MU, S>.
+template <int MU, int S>
+__device__ __forceinline__ void project_h16(const uint32_t (&p)[12], Cx<float> (&h)[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (MU == 0) {
+            h[0][a] = hadd_si<S>(p[a], h2cx(p[9 + a]));
+            h[1][a] = hadd_si<S>(p[3 + a], h2cx(p[6 + a]));
+        } else if constexpr (MU == 1) {
+            h[0][a] = hadd_s<-S>(p[a], h2cx(p[9 + a]));
+            h[1][a] = hadd_s<S>(p[3 + a], h2cx(p[6 + a]));
+        } else if constexpr (MU == 2) {
+            h[0][a] = hadd_si<S>(p[a], h2cx(p[6 + a]));
+            h[1][a] = hadd_si<-S>(p[3 + a], h2cx(p[9 + a]));
+        } else {
+            h[0][a] = hadd_s<S>(p[a], h2cx(p[6 + a]));
+            h[1][a] = hadd_s<S>(p[3 + a], h2cx(p[9 + a]));
+        }
+    }
+}
+
+// Raw bytes of one hop (neighbour spinor, its FP16 scale, the link) as
+// loaded from memory, before any conversion.
+template <int P, int RECON>
+struct HopRaw {
+    using L = HopLayout<P, RECON>;
+    using LinkWord = typename std::conditional<L::link_bytes == 16, uint4, uint2>::type;
+    uint4 spin[L::spin16];
+    float scale;
+    LinkWord link[L::link_chunks];
+};
+
+template <int P, int RECON>
+__device__ __forceinline__ HopRaw<P, RECON> stage_load_raw(const Stage<P, RECON> &st, int tid) {
+    using H = HopRaw<P, RECON>;
+    H r;
+#pragma unroll
+    for (int k = 0; k < H::L::spin16; ++k) r.spin[k] = *st.spin(k, tid);
+    r.scale = H::L::scale4 ? *st.scale(tid) : 1.0f;
+#pragma unroll
+    for (int k = 0; k < H::L::link_chunks; ++k) r.link[k] = *reinterpret_cast<const typename H::LinkWord *>(st.link(k, tid));
+    return r;
+}
+
+// Hop J of output site c from its raw bytes: projection, link (third row
+// rebuilt for recon 12), SU(3) product, boundary phase, accumulation.
 template <int P, int RECON, int J, bool DAGGER>
-__device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c, const Stage<P, RECON> &st,
-                                              int tid, Cx<float> (&acc)[12], float bs) {
+__device__ __forceinline__ void hop_compute(const Geom &g, const Coord &c, const HopRaw<P, RECON> &r,
+                                            Cx<float> (&acc)[12], float bs) {
     using L = HopLayout<P, RECON>;
     constexpr int MU = Hop<J>::MU, DIR = Hop<J>::DIR;
     constexpr int SF = DAGGER ? +1 : -1;
     constexpr int S = DIR > 0 ? SF : -SF;
-    const Geom &g = A.g;
-    Cx<float> psi[12];
     float sc = bs;
+    Cx<float> h[2][3];
     if constexpr (P == COLA_F16) {
+        uint32_t raw[12];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const uint4 v = *st.spin(k, tid);
-            float2 a = h2f(v.x), b = h2f(v.y), cc = h2f(v.z), d = h2f(v.w);
-            psi[4 * k + 0] = {a.x, a.y};
-            psi[4 * k + 1] = {b.x, b.y};
-            psi[4 * k + 2] = {cc.x, cc.y};
-            psi[4 * k + 3] = {d.x, d.y};
+            raw[4 * k + 0] = r.spin[k].x;
+            raw[4 * k + 1] = r.spin[k].y;
+            raw[4 * k + 2] = r.spin[k].z;
+            raw[4 * k + 3] = r.spin[k].w;
         }
-        sc *= *st.scale(tid);
+        sc *= r.scale;
+        project_h16<MU, S>(raw, h);
     } else {
+        Cx<float> psi[12];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const float4 v = *reinterpret_cast<const float4 *>(st.spin(k, tid));
+            const float4 v = *reinterpret_cast<const float4 *>(&r.spin[k]);
             psi[2 * k] = {v.x, v.y};
             psi[2 * k + 1] = {v.z, v.w};
         }
+        project<MU, S>(psi, h);
     }
-    Cx<float> h[2][3];
-    project<MU, S>(psi, h);
     Cx<float> u[9];
     if constexpr (P == COLA_F16) {
 #pragma unroll
         for (int k = 0; k < L::link_chunks; ++k) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(st.link(k, tid));
+            const uint2 v = *reinterpret_cast<const uint2 *>(&r.link[k]);
             float2 a = h2f(v.x), b = h2f(v.y);
             if (2 * k < 9) u[2 * k] = {a.x, a.y};
             if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
@@ -397,7 +555,7 @@ __device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c
     } else {
 #pragma unroll
         for (int k = 0; k < L::link_chunks; ++k) {
-            const float4 v = *reinterpret_cast<const float4 *>(st.link(k, tid));
+            const float4 v = *reinterpret_cast<const float4 *>(&r.link[k]);
             if (2 * k < 9) u[2 * k] = {v.x, v.y};
             if (2 * k + 1 < 9) u[2 * k + 1] = {v.z, v.w};
         }
@@ -408,6 +566,12 @@ __device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c
     else su3_adj_mul(u, h, w);
     if (!g.bc_trivial[MU] && coord_of<MU>(c) == (DIR > 0 ? g.L[MU] - 1 : 0)) boundary_phase(g, MU, DIR < 0, w, sc);
     accumulate<MU, S>(acc, w, sc);
+}
+
+template <int P, int RECON, int J, bool DAGGER>
+__device__ __forceinline__ void stage_compute(const DslashLat &A, const Coord &c, const Stage<P, RECON> &st,
+                                              int tid, Cx<float> (&acc)[12], float bs) {
+    hop_compute<P, RECON, J, DAGGER>(A.g, c, stage_load_raw(st, tid), acc, bs);
 }
 
 template <int P, int RECON, bool DAGGER, int NS, int J>
@@ -524,6 +688,80 @@ __global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS
         SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb, acc);
 }
 
+// Multi-right-hand-side variant (direct loads): each thread carries NR
+// right-hand sides of one site, so every link is loaded and reconstructed
+// once per NR outputs.  Grid x runs over (site block, right-hand-side group)
+// pairs as in dslash_kernel; a group is blockDim.y x NR right-hand sides.
+template <int P, int RECON, bool DAGGER, int EPI, int NR>
+__global__ void __launch_bounds__(256, 1) dslash_mrhs_kernel(const __grid_constant__ DslashArgs A) {
+    using R = typename Prec<P>::real;
+    int l = 0;
+    while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
+    const DslashLat &L = A.lat[l];
+    const Geom &g = L.g;
+    const int rel = (int)blockIdx.x - L.block0;
+    const int grp = A.ngroups == 1 ? 0 : rel % A.ngroups;
+    const int sblk = A.ngroups == 1 ? rel : rel / A.ngroups;
+    const int cb = sblk * blockDim.x + threadIdx.x;
+    const int rhs0 = (grp * blockDim.y + threadIdx.y) * NR;
+    const int par = A.parity0 + blockIdx.z;
+    if (cb >= g.Vh) return;
+    bool live[NR];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int rhs = rhs0 + k;
+        bool ok = rhs < A.nrhs;
+        if (ok && A.state) {
+            const CgState &st = A.state[L.row0 + rhs];
+            ok = A.filter_ru ? (st.ru && !st.done) : !st.done;
+        }
+        live[k] = ok;
+        any |= ok;
+    }
+    if (!any) return;
+    const Coord c = cb_coord(g, cb, par);
+    const char *in0 = static_cast<const char *>(L.in) + (size_t)rhs0 * L.rhs_stride + (1 - par) * L.parity_stride;
+    const char *lo = static_cast<const char *>(L.links) + par * L.link_parity_stride;
+    const char *li = static_cast<const char *>(L.links) + (1 - par) * L.link_parity_stride;
+    Cx<R> acc[NR][12];
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int j = 0; j < 12; ++j) acc[k][j] = {R(0), R(0)};
+    hop_mu_mrhs<P, RECON, 0, DAGGER, NR>(L, c, cb, in0, lo, li, acc, (R)L.b, live);
+    hop_mu_mrhs<P, RECON, 1, DAGGER, NR>(L, c, cb, in0, lo, li, acc, (R)L.b, live);
+    hop_mu_mrhs<P, RECON, 2, DAGGER, NR>(L, c, cb, in0, lo, li, acc, (R)L.b, live);
+    hop_mu_mrhs<P, RECON, 3, DAGGER, NR>(L, c, cb, in0, lo, li, acc, (R)L.b, live);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        if (!live[k]) continue;
+        const size_t roff = (size_t)(rhs0 + k) * L.rhs_stride + par * L.parity_stride;
+        if constexpr (EPI == EPI_XPAY || EPI == EPI_CLOVER_X) {
+            const R a = (R)L.a;
+            Cx<R> xs[12];
+            SpinorIO<P>::load(static_cast<const char *>(L.xin) + roff, g.Vh, cb, xs);
+            if constexpr (EPI == EPI_CLOVER_X)
+                clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, xs);
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                acc[k][j].re = fma(a, xs[j].re, acc[k][j].re);
+                acc[k][j].im = fma(a, xs[j].im, acc[k][j].im);
+            }
+        }
+        if constexpr (EPI == EPI_CLOVER_INV)
+            clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, acc[k]);
+        SpinorIO<P>::store(static_cast<char *>(L.out) + roff, g.Vh, cb, acc[k]);
+    }
+}
+
+// Right-hand sides per thread the multi-right-hand-side kernel is built for
+// (FP32 storage, direct loads); other precisions and the staged kernels carry
+// one right-hand side per thread.
+__host__ __device__ constexpr bool mrhs_supported(int prec, int nr) {
+    return nr == 1 || (prec == COLA_F32 && (nr == 2 || nr == 4));
+}
+
 // Pipeline depth of the staged kernels: FP16 storage moves half the bytes
 // per load of FP32, so it needs the deeper pipeline; FP32 keeps direct loads
 // (measured on GB300 at 32^3x64).  COLA_DSLASH_STAGES=0 or 3 overrides.
@@ -556,8 +794,21 @@ static cudaError_t launch_ns(const DslashArgs &A, int nparity, int bx, int total
     return cudaGetLastError();
 }
 
+template <int P, int RECON, bool DAGGER, int EPI, int NR>
+static cudaError_t launch_mrhs(const DslashArgs &A, int nparity, int bx, int total_blocks, cudaStream_t s) {
+    dim3 block(bx, A.rhs_per_block, 1);
+    dim3 grid(total_blocks, 1, nparity);
+    dslash_mrhs_kernel<P, RECON, DAGGER, EPI, NR><<<grid, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 template <int P, int RECON, bool DAGGER, int EPI>
 static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cudaStream_t s) {
+    if constexpr (P == COLA_F32) {
+        if (A.rhs_per_thread == 2) return launch_mrhs<P, RECON, DAGGER, EPI, 2>(A, nparity, bx, nb, s);
+        if (A.rhs_per_thread == 4) return launch_mrhs<P, RECON, DAGGER, EPI, 4>(A, nparity, bx, nb, s);
+    }
+    if (A.rhs_per_thread > 1) return cudaErrorInvalidValue;
     if constexpr (P == COLA_F64) {
         return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
     } else {

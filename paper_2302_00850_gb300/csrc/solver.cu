@@ -334,9 +334,11 @@ cola_status check_params(const cola_solver_params *prm) {
 // shifts (host, nrhs entries, may be null): right-hand side r solves
 // (A + shifts[r]) x = b (normal system only).  shared_b: bs[l] holds one field
 // that every right-hand side of lattice l solves with.
-cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const void *const *bs,
-                        const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s,
-                        const double *shifts = nullptr, bool shared_b = false) {
+// row_tol / row_max_iter (host, one per row, may be null): per-row overrides
+// of prm->tol and prm->max_iter for the CG's stopping test.
+cola_status solve_batch_pass(int nlat, const cola_gauge *gs, void *const *xs, const void *const *bs,
+                             const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s,
+                             const double *shifts, bool shared_b, const double *row_tol, const int *row_max_iter) {
     const auto t0 = std::chrono::steady_clock::now();
     COLA_TRY(check_params(prm));
     if (shifts && prm->system != COLA_SYS_NORMAL) return arg_error("shifted solves need the normal system");
@@ -442,9 +444,10 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
     for (int r = 0; r < nrows; ++r) {
         CgState &st = hs[r];
         std::memset(&st, 0, sizeof(st));
-        st.tol2 = prm->tol * prm->tol;
+        const double tol = row_tol ? row_tol[r] : prm->tol;
+        st.tol2 = tol * tol;
         st.delta2 = prm->inner == COLA_F64 ? 0.0 : prm->delta * prm->delta;
-        st.max_iter = prm->max_iter;
+        st.max_iter = row_max_iter ? row_max_iter[r] : prm->max_iter;
         st.shift = shifts ? shifts[r % c.nrhs] : 0.0;
         st.status = COLA_ERR_NOT_CONVERGED;
     }
@@ -579,6 +582,58 @@ cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const v
             log_line("cg_solve row %d: status %d, %d iterations, %d reliable updates, true residual %.3e, %.3f s", r,
                      info[r].status, info[r].iters, info[r].reliable_updates, info[r].true_rel_resid, secs);
     return worst;
+}
+
+// Passes of the Dirac-system refinement before a row that still misses the
+// tolerance is reported as not converged.
+constexpr int kDiracPasses = 6;
+
+// The Dirac system D x = b is solved through the normal equations (of Mhat on
+// the even sites, or of D), whose CG stops on the normal-equation residual;
+// the contract is the Dirac residual |b - D x| <= tol |b|.  So every row whose
+// Dirac residual is still above tol is solved again from its current x with
+// the normal-equation target scaled down by the ratio it missed by (halved
+// again for margin), until every row meets tol.  Rows that already meet it
+// start below their target and stop at once.  Iterations, reliable updates
+// and seconds are summed over the passes.
+cola_status solve_batch(int nlat, const cola_gauge *gs, void *const *xs, const void *const *bs,
+                        const cola_solver_params *prm, cola_solve_info *info, cudaStream_t s,
+                        const double *shifts = nullptr, bool shared_b = false) {
+    if (prm->system != COLA_SYS_DIRAC)
+        return solve_batch_pass(nlat, gs, xs, bs, prm, info, s, shifts, shared_b, nullptr, nullptr);
+    COLA_TRY(check_params(prm));
+    if (shifts) return arg_error("shifted solves need the normal system");
+    const int nrows = nlat * prm->nrhs;
+    std::vector<double> tol(nrows, prm->tol);
+    std::vector<int> maxit(nrows, prm->max_iter);
+    std::vector<cola_solve_info> cur(nrows);
+    for (int r = 0; r < nrows; ++r) info[r] = {0, 0, -1.0, 0.0, COLA_ERR_NOT_CONVERGED};
+    for (int pass = 0;; ++pass) {
+        const cola_status st = solve_batch_pass(nlat, gs, xs, bs, prm, cur.data(), s, nullptr, false, tol.data(),
+                                                maxit.data());
+        if (st != COLA_OK && st != COLA_ERR_NOT_CONVERGED && st != COLA_ERR_BREAKDOWN) return st;
+        bool again = false;
+        for (int r = 0; r < nrows; ++r) {
+            info[r].iters += cur[r].iters;
+            info[r].reliable_updates += cur[r].reliable_updates;
+            info[r].seconds += cur[r].seconds;
+            info[r].true_rel_resid = cur[r].true_rel_resid;
+            info[r].status = cur[r].status;
+            maxit[r] = std::max(0, maxit[r] - cur[r].iters);
+            if (cur[r].status == COLA_OK && !(cur[r].true_rel_resid <= prm->tol)) {
+                again = true;
+                tol[r] *= std::max(0.5 * prm->tol / cur[r].true_rel_resid, 1e-4);
+            }
+        }
+        if (!again) return st;
+        if (pass + 1 == kDiracPasses) {
+            for (int r = 0; r < nrows; ++r)
+                if (info[r].status == COLA_OK && !(info[r].true_rel_resid <= prm->tol))
+                    info[r].status = COLA_ERR_NOT_CONVERGED;
+            set_error("Dirac-system solve: the Dirac residual stayed above tol after refinement passes");
+            return COLA_ERR_NOT_CONVERGED;
+        }
+    }
 }
 
 }  // namespace

@@ -5,8 +5,9 @@
   times; its true relative residual is recomputed by the oracle's own
   whole-lattice operator.
 * 24^3x48, kappa 0.124, links exp(0.3 i H), phi = D^dag eta: the fermion force
-  from a GPU solve, compared with the oracle's force of the same X, Y on
-  sampled links (the oracle formula evaluated link by link).
+  through the autograd backward, checked by central finite differences of the
+  action and by the closed form S = |eta|^2; the force kernel on seeded X, Y
+  against the oracle's formula evaluated link by link.
 """
 import numpy as np
 import pytest
@@ -73,28 +74,87 @@ def _force_at_links(u, X, Y, kappa, bc, links):
     return np.array(out)
 
 
-def test_force_24x24x24x48_sampled_links(cola):
+def test_force_24x24x24x48_autograd_fd_and_oracle(cola):
+    """The HMC force workload as configured: 24^3x48, kappa 0.124, links
+    exp(0.3 i H), phi = D^dag eta with eta standard complex Gaussian.
+
+    * The link gradient comes from PseudofermionAction.backward (the autograd
+      path), FP64 force accumulation, projected onto the generators T^a.
+    * Central finite differences of the action along a random su(3) field
+      omega (U -> exp(+-i eps omega.T) U, eps = 1e-6, perturbed links by the
+      oracle's exponential) must match sum F.omega to 1e-5 relative.  The
+      action is the variational estimator S~ = 2 Re<phi, X~> - |D X~|^2 from
+      FP64 GPU solves to 1e-12, whose error is quadratic in the residual.
+    * At the base point S = |eta|^2 exactly.
+    * The force kernel, on seeded X and Y (inputs independent of the GPU
+      path), matches the oracle's force formula on sampled links to 1e-13;
+      the projected autograd gradient equals that kernel on the solve's own
+      X and Y = D X.
+    """
+    import torch
+
     dims = (24, 24, 24, 48)
     kappa = 0.124
     u_dev = synth.gauge_field(dims, 0.3, synth.seed_for(4, 0), device="cuda", as_numpy=False)
-    eta = synth.gaussian_spinor(dims, synth.seed_for(4, 1))
-    g = cola.Gauge(u_dev, dims, kappa, BC_AP, precisions=("f64", "f32"), recon={"f64": 18, "f32": 12})
-    phi = cola.apply_dirac(g, to_dev(eta), dagger=True)
-    X, info = cola.cg_solve(g, phi, tol=1e-10, op="full", inner="f32", delta=0.1, use_graph=True)
-    assert info[0].status == 0
-    Y = cola.apply_dirac(g, X)
-    F = cola.fermion_force(g, X, Y).cpu().numpy().reshape(4, -1, 8)
     u = u_dev.cpu().numpy()
-    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    eta = synth.gaussian_spinor(dims, synth.seed_for(4, 1))
+    phi_np = oracle.dirac_dag(u, eta, kappa, BC_AP)
+    phi = to_dev(phi_np)
+
+    # autograd: dS/dU from PseudofermionAction.backward
+    links = u_dev.clone().requires_grad_(True)
+    S = cola.PseudofermionAction.apply(links, phi, dims, kappa, BC_AP, 1e-12, "f32")
+    S.backward()
+    G = links.grad
+    T = torch.from_numpy(oracle.T_GEN).to("cuda")
+    F_auto = torch.stack([torch.real(torch.sum(G.conj() * (1j * torch.einsum("ab,...bc->...ac", T[a], u_dev)),
+                                               dim=(-2, -1))) for a in range(8)], dim=-1)
+    F_auto = F_auto.cpu().numpy()  # [4, Lt, Lz, Ly, Lx, 8]
+    del G, links
+    eta2 = float(np.sum(np.abs(eta) ** 2))
+    assert abs(S.item() - eta2) < 1e-8 * eta2
+
+    # the force kernel on the solve's own X, Y = D X equals the projected gradient
+    g = cola.Gauge(u_dev, dims, kappa, BC_AP, precisions=("f64",), recon={"f64": 18})
+
+    def s_var(gg):
+        x, info = cola.cg_solve(gg, phi, tol=1e-12, op="full", inner="f64", use_graph=True)
+        assert info[0].status == 0 and info[0].true_rel_resid <= 1e-12
+        dx = cola.apply_dirac(gg, x)
+        return (2 * torch.vdot(phi.reshape(-1), x.reshape(-1)).real
+                - torch.vdot(dx.reshape(-1), dx.reshape(-1)).real).item(), x, dx
+
+    s0, X, Y = s_var(g)
+    assert abs(s0 - eta2) < 1e-10 * eta2  # closed form at phi = D^dag eta
+    F = cola.fermion_force(g, X, Y).cpu().numpy()
+    assert rel_err(F_auto, F) < 1e-9
+    del X, Y
+
+    # central finite differences along omega
+    omega = synth.su3_direction(dims, synth.seed_for(4, 2))
+    eps = 1e-6
+    s = []
+    for sgn in (+1, -1):
+        gp = cola.Gauge(to_dev(oracle.link_variation(u, omega, sgn * eps)), dims, kappa, BC_AP,
+                        precisions=("f64",), recon={"f64": 18})
+        s.append(s_var(gp)[0])
+        del gp
+    fd = (s[0] - s[1]) / (2 * eps)
+    an = float(np.sum(F_auto * omega))
+    assert abs(fd - an) < 1e-5 * abs(an), (fd, an)
+
+    # the force kernel against the oracle formula on seeded X, Y at sampled links
+    Xs = synth.gaussian_spinor(dims, synth.seed_for(4, 3))
+    Ys = synth.gaussian_spinor(dims, synth.seed_for(4, 4))
+    Fs = cola.fermion_force(g, to_dev(Xs), to_dev(Ys)).cpu().numpy().reshape(4, -1, 8)
     v = 24 ** 3 * 48
     rng = np.random.default_rng(11)
-    links = [(3, v - 1), (3, 0), (0, 23), (1, 24 * 23)] + [(int(m), int(s)) for m, s in
-                                                            zip(rng.integers(0, 4, 300), rng.integers(0, v, 300))]
-    want = _force_at_links(u, Xn, Yn, kappa, BC_AP, links)
-    got = np.array([F[m, s] for m, s in links])
+    sampled = [(3, v - 1), (3, 0), (0, 23), (1, 24 * 23)] + [(int(m), int(i)) for m, i in
+                                                              zip(rng.integers(0, 4, 300), rng.integers(0, v, 300))]
+    want = _force_at_links(u, Xs, Ys, kappa, BC_AP, sampled)
+    got = np.array([Fs[m, i] for m, i in sampled])
     assert rel_err(got, want) < 1e-13
-    # Y = D X and the phi = D^dag eta structure: X is the solution of D^dag D X = D^dag eta, so D X = eta
-    assert rel_err(Yn, eta) < 1e-8
+    torch.cuda.empty_cache()
 
 
 def _eo_resid(u, x, b, kappa, dims):

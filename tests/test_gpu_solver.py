@@ -98,7 +98,7 @@ def test_dirac_system_eo_and_full(cola, inner):
         x, info = cola.cg_solve(g, to_dev(b), tol=1e-11, op=op, system="dirac", inner=inner)
         x = x.cpu().numpy()
         res = rel_err(oracle.dirac(u, x, kappa, BC_AP), b)
-        assert res < 1e-9 and abs(res - info[0].true_rel_resid) < 1e-11
+        assert res <= 1e-11 and abs(res - info[0].true_rel_resid) < 1e-13
         assert rel_err(x, x_ref) < 1e-8
 
 
