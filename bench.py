@@ -552,11 +552,12 @@ def run_cola(args):
     value = flops / (t_ms * 1e-3) / 1e9
     # kernels per solve: 9 set-up/finish launches (packing, |b|^2 and its
     # finishing kernel, the zero-guess check, initial residual and finisher,
-    # final accumulate, unpacking), 11 per iteration (4 Dslash, <p,Ap> and
-    # x/r update each with a finishing kernel, p update, 2 graph-control
-    # kernels) and 7 per reliable update after the first (accumulate, 4 FP64
-    # Dslash, residual and its finishing kernel)
-    launches = sum(9 + 11 * it + 7 * (ru - 1) for it, ru in zip(iters, rus))
+    # final accumulate, unpacking), 10 per iteration (4 Dslash, the last of
+    # which also reduces <p,Ap>, its finishing kernel, the x/r update and its
+    # finishing kernel, the p update, 2 graph-control kernels) and 7 per
+    # reliable update after the first (accumulate, 4 FP64 Dslash, residual
+    # and its finishing kernel)
+    launches = sum(9 + 10 * it + 7 * (ru - 1) for it, ru in zip(iters, rus))
 
     # plain FP64 CG on the same inputs (the comparison of the metric)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -916,9 +917,11 @@ def clover_measurements(cola, dev, u, b):
 # each, the product U V, and the staple sums (3x3 complex product = 27 complex
 # multiply-adds = 216 flop)
 GAUGE_FORCE_FLOP_PER_LINK = 13 * 216 + 5 * 18
-# clover force per link: for each of the three planes through it, 9 products
-# of 3x3 complex matrices per plaquette (two plaquettes), then U S+ and S- U^dag
-CLOVER_FORCE_FLOP_PER_LINK = (3 * 2 * 9 + 2) * 216
+# clover force per link (18-real FP64 links): for each of the three planes
+# through it, two plaquettes of 8 products of 3x3 complex matrices each in
+# nested form, 4 of them with the Hermitian insertion matrix (real diagonal:
+# 180 instead of 216 flop), then U S+ and S- U^dag
+CLOVER_FORCE_FLOP_PER_LINK = 3 * 2 * (4 * 216 + 4 * 180) + 2 * 216
 
 
 def hmc_measurements(cola, dev):

@@ -203,7 +203,7 @@ typedef struct {
 typedef struct {
     int iters;             /* CG iterations */
     int reliable_updates;  /* FP64 residual recomputations, the initial one included */
-    double true_rel_resid; /* |b - A x| / |b| recomputed in FP64 at the end */
+    double true_rel_resid; /* |b - A x| / |b| (SYS_DIRAC: |b - D x| / |b|) recomputed in FP64 at the end */
     double seconds;        /* wall time of the call */
     int status;            /* cola_status of this right-hand side */
 } cola_solve_info;
@@ -214,8 +214,14 @@ typedef struct {
  * Mhat^dag Mhat x_e = b_e (odd sites of b ignored, of x set to zero).
  * SYS_DIRAC: D x = b (OP_EO through the Schur complement and its normal
  * equations, x_o = A_oo^-1 (b_o + kappa H_oe x_e), A = 1 without a clover
- * term).  info has nrhs entries (host).  With clover terms, every handle of
- * a batched solve must have one. */
+ * term).  Convergence is declared on the FP64 true residual of the system
+ * solved: |b - A x| <= tol |b| for SYS_NORMAL; for SYS_DIRAC on the Dirac
+ * residual |b - D x| <= tol |b| over the whole lattice (a right-hand side
+ * whose normal equations met their target while its Dirac residual did not
+ * is solved again from its x with a target scaled down by the ratio it
+ * missed by; iters and reliable_updates then sum the passes, and after 6
+ * passes it returns COLA_ERR_NOT_CONVERGED).  info has nrhs entries (host).
+ * With clover terms, every handle of a batched solve must have one. */
 cola_status cola_cg_solve(cola_gauge g, void *x_dev, const void *b_dev,
                           const cola_solver_params *params, cola_solve_info *info,
                           cudaStream_t stream);

@@ -206,7 +206,7 @@ cola_status dslash_launch(cola_gauge owner, int prec, DslashArgs &A, int nparity
 // the A_oo^-1 riding on the odd-parity hops (EPI_CLOVER_INV) and A on the
 // xpay term (EPI_CLOVER_X); the sequence of launches is the same.
 cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
-                              cudaStream_t s) {
+                              cudaStream_t s, double *red, int red_stride, int *red_nb) {
     cola_gauge owner = L[0].g;
     const bool clv = owner->csw != 0.0;
     const int epi_x = clv ? EPI_CLOVER_X : EPI_XPAY;
@@ -236,13 +236,23 @@ cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nr
         COLA_TRY(dslash_launch(owner, prec, A, 1, false, epi_x, s));
         A = batch(1, 0.0, false, 2);
         COLA_TRY(dslash_launch(owner, prec, A, 1, true, epi_h, s));
-        A = batch(0, 1.0, true, 3);
-        return dslash_launch(owner, prec, A, 1, true, epi_x, s);
+        A = batch(0, 1.0, true, 3);  // xin = Mhat in: the fused reduction gives |Mhat in|^2
+        A.red = red;
+        A.red_stride = red_stride;
+        COLA_TRY(dslash_launch(owner, prec, A, 1, true, epi_x, s));
+        if (red_nb)
+            for (int l = 0; l < nlat; ++l) red_nb[l] = A.lat[l].nblocks;
+        return COLA_OK;
     }
     DslashArgs A = batch(0, 1.0, true, 4);
     COLA_TRY(dslash_launch(owner, prec, A, 2, false, epi_x, s));
-    A = batch(0, 1.0, true, 5);
-    return dslash_launch(owner, prec, A, 2, true, epi_x, s);
+    A = batch(0, 1.0, true, 5);  // xin = D in: the fused reduction gives |D in|^2
+    A.red = red;
+    A.red_stride = red_stride;
+    COLA_TRY(dslash_launch(owner, prec, A, 2, true, epi_x, s));
+    if (red_nb)
+        for (int l = 0; l < nlat; ++l) red_nb[l] = 2 * A.lat[l].nblocks;
+    return COLA_OK;
 }
 
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,

@@ -12,6 +12,8 @@
 // solves give identical results.  Every kernel walks one table of lattices
 // (a batch of up to kMaxBatch lattices, each with nrhs right-hand sides), so
 // a batch of uneven lattices is one launch per step.
+#include <algorithm>
+
 #include "cola_impl.h"
 
 namespace cola {
@@ -421,6 +423,14 @@ cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s) {
     else cg_pq_kernel<COLA_F16><<<g, kBlasBlock, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     return e != cudaSuccess ? e : finish<FIN_PQ>(B, s);
+}
+
+cudaError_t launch_finish_pq(const BlasArgs &B, cudaStream_t s) { return finish<FIN_PQ>(B, s); }
+
+int reduce_stride(int vh) {
+    // vector kernels: 256 sites per block over both parities; hopping
+    // launches: at least 32 sites per block, both parities
+    return std::max((2 * vh + kBlasBlock - 1) / kBlasBlock, 2 * ((vh + 31) / 32));
 }
 
 cudaError_t launch_ru_accumulate(BlasArgs &B, bool force, cudaStream_t s) {

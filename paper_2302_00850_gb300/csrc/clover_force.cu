@@ -143,6 +143,52 @@ __device__ __forceinline__ void mac3(C64 (&acc)[9], const C64 (&a)[9], const C64
         }
 }
 
+// Products with the insertion matrix G (Hermitian, so its diagonal is real:
+// only the real parts of g[0], g[4], g[8] are read), which saves the two
+// multiply-adds by the zero imaginary parts of each diagonal entry.
+// acc (+)= G b
+template <bool ACC>
+__device__ __forceinline__ void gmul_left(C64 (&acc)[9], const C64 (&gm)[9], const C64 (&b)[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double d = gm[4 * i].re;
+            C64 s = ACC ? acc[3 * i + j] : C64{0.0, 0.0};
+            s.re = fma(d, b[3 * i + j].re, s.re);
+            s.im = fma(d, b[3 * i + j].im, s.im);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k != i) cmac(s, gm[3 * i + k], b[3 * k + j]);
+            acc[3 * i + j] = s;
+        }
+}
+// acc (+)= a G
+template <bool ACC>
+__device__ __forceinline__ void gmul_right(C64 (&acc)[9], const C64 (&a)[9], const C64 (&gm)[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double d = gm[4 * j].re;
+            C64 s = ACC ? acc[3 * i + j] : C64{0.0, 0.0};
+            s.re = fma(a[3 * i + j].re, d, s.re);
+            s.im = fma(a[3 * i + j].im, d, s.im);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k != j) cmac(s, a[3 * i + k], gm[3 * k + j]);
+            acc[3 * i + j] = s;
+        }
+}
+
+// The specialised products where registers allow: with 12-real links the
+// third-row reconstruction's temporaries leave no room for them without
+// spilling, so those builds use the general products.
+template <int RECON, bool ACC>
+__device__ __forceinline__ void g_left(C64 (&acc)[9], const C64 (&gm)[9], const C64 (&b)[9]);
+template <int RECON, bool ACC>
+__device__ __forceinline__ void g_right(C64 (&acc)[9], const C64 (&a)[9], const C64 (&gm)[9]);
+
 __device__ __forceinline__ void adj3(C64 (&m)[9]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -154,6 +200,19 @@ __device__ __forceinline__ void adj3(C64 (&m)[9]) {
             m[3 * j + i] = {a.re, -a.im};
         }
     }
+}
+
+template <int RECON, bool ACC>
+__device__ __forceinline__ void g_left(C64 (&acc)[9], const C64 (&gm)[9], const C64 (&b)[9]) {
+    if constexpr (RECON == 18) gmul_left<ACC>(acc, gm, b);
+    else if constexpr (ACC) mac3(acc, gm, b);
+    else mul3(gm, b, acc);
+}
+template <int RECON, bool ACC>
+__device__ __forceinline__ void g_right(C64 (&acc)[9], const C64 (&a)[9], const C64 (&gm)[9]) {
+    if constexpr (RECON == 18) gmul_right<ACC>(acc, a, gm);
+    else if constexpr (ACC) mac3(acc, a, gm);
+    else mul3(a, gm, acc);
 }
 
 // op(U_dir(y + dmu mu + dnu nu)), op = identity or adjoint
@@ -200,41 +259,44 @@ __global__ void __launch_bounds__(128) clover_force_kernel(const Geom g, const c
         if (nu == mu) continue;
         const int plane = mu < nu ? plane_of(mu, nu) : plane_of(nu, mu);
         const double sign = mu < nu ? 1.0 : -1.0;
-        C64 a[9], b[9], d[9], gm[9], t[9];
+        // Each side's insertion sum in nested (Horner) form, 8 products of
+        // 3x3 matrices instead of 9:
+        //   S+ += L2 (L3 (L4 G(y) + G(y+nu) L4) + G(y+mu+nu) L3 L4) + G(y+mu) L2 L3 L4
+        //   S- += M1 (M2 (G(y-nu+mu) M3 + M3 G(y+mu)) + G(y-nu) M2 M3) + G(y) M1 M2 M3
+        C64 l2[9], l3[9], l4[9], gm[9], t[9], u[9];
         // ---- the plaquette on the +nu side: L2 = U_nu(y+mu), L3 = U_mu(y+nu)^dag, L4 = U_nu(y)^dag
-        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, 0, false, a);  // L2
-        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, 1, true, b);   // L3
-        mul3(a, b, d);                                                         // L2 L3
-        gam_off(g, gam, plane, sign, c, mu, 1, nu, 1, gm);                     // G(y+mu+nu)
-        mul3(a, gm, t);                                                        // L2 G
-        mul3(t, b, a);                                                         // L2 G L3 (a free)
-        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, 0, true, b);   // L4 (L3 free)
-        mac3(sp, a, b);                                                        // + L2 G(y+mu+nu) L3 L4
-        gam_off(g, gam, plane, sign, c, mu, 0, nu, 1, gm);                     // G(y+nu)
-        mul3(d, gm, t);
-        mac3(sp, t, b);                                                        // + L2 L3 G(y+nu) L4
-        mul3(d, b, a);                                                         // L2 L3 L4
-        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                     // G(y)
-        mac3(sp, a, gm);                                                       // + L2 L3 L4 G(y)
-        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                     // G(y+mu)
-        mac3(sp, gm, a);                                                       // + G(y+mu) L2 L3 L4
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, 0, true, l4);   // L4
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                      // G(y)
+        g_right<RECON, false>(t, l4, gm);                                       // L4 G(y)
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 1, gm);                      // G(y+nu)
+        g_left<RECON, true>(t, gm, l4);                                          // + G(y+nu) L4
+        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, 1, true, l3);   // L3
+        mul3(l3, t, u);                                                         // L3 (...)
+        mul3(l3, l4, t);                                                        // L3 L4
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 1, gm);                      // G(y+mu+nu)
+        g_left<RECON, true>(u, gm, t);                                           // + G(y+mu+nu) L3 L4
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, 0, false, l2);  // L2
+        mac3(sp, l2, u);                                                        // S+ += L2 (...)
+        mul3(l2, t, u);                                                         // L2 L3 L4
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                      // G(y+mu)
+        g_left<RECON, true>(sp, gm, u);                                          // S+ += G(y+mu) L2 L3 L4
         // ---- the plaquette on the -nu side: M1 = U_nu(y-nu)^dag, M2 = U_mu(y-nu), M3 = U_nu(y-nu+mu)
-        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, -1, true, a);  // M1
-        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, -1, false, b); // M2
-        mul3(a, b, d);                                                         // M1 M2
-        gam_off(g, gam, plane, sign, c, mu, 0, nu, -1, gm);                    // G(y-nu)
-        mul3(a, gm, t);                                                        // M1 G
-        mul3(t, b, a);                                                         // M1 G M2 (a free)
-        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, -1, false, b); // M3 (M2 free)
-        mac3(sm, a, b);                                                        // + M1 G(y-nu) M2 M3
-        gam_off(g, gam, plane, sign, c, mu, 1, nu, -1, gm);                    // G(y-nu+mu)
-        mul3(d, gm, t);
-        mac3(sm, t, b);                                                        // + M1 M2 G(y-nu+mu) M3
-        mul3(d, b, a);                                                         // M1 M2 M3
-        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                     // G(y)
-        mac3(sm, gm, a);                                                       // + G(y) M1 M2 M3
-        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                     // G(y+mu)
-        mac3(sm, a, gm);                                                       // + M1 M2 M3 G(y+mu)
+        // (M1, M2, M3 reuse the registers of L2, L3, L4)
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 1, nu, -1, false, l4); // M3
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, -1, gm);                     // G(y-nu+mu)
+        g_left<RECON, false>(t, gm, l4);                                         // G(y-nu+mu) M3
+        gam_off(g, gam, plane, sign, c, mu, 1, nu, 0, gm);                      // G(y+mu)
+        g_right<RECON, true>(t, l4, gm);                                         // + M3 G(y+mu)
+        link_off<RECON>(g, links, dir_stride, c, mu, mu, 0, nu, -1, false, l3); // M2
+        mul3(l3, t, u);                                                         // M2 (...)
+        mul3(l3, l4, t);                                                        // M2 M3
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, -1, gm);                     // G(y-nu)
+        g_left<RECON, true>(u, gm, t);                                           // + G(y-nu) M2 M3
+        link_off<RECON>(g, links, dir_stride, c, nu, mu, 0, nu, -1, true, l2);  // M1
+        mac3(sm, l2, u);                                                        // S- += M1 (...)
+        mul3(l2, t, u);                                                         // M1 M2 M3
+        gam_off(g, gam, plane, sign, c, mu, 0, nu, 0, gm);                      // G(y)
+        g_left<RECON, true>(sm, gm, u);                                          // S- += G(y) M1 M2 M3
     }
     if constexpr (GRAD) {
         double2 *o = static_cast<double2 *>(out) + ((size_t)mu * g.V + i) * 9;

@@ -42,6 +42,12 @@ struct DslashArgs {
     CgState *state;               // solver mode: skip finished rows
     int filter_ru;                // with state: compute only rows with a pending reliable update
     int ngroups;                  // right-hand-side groups (set by launch_dslash)
+    // With red != null (xpay epilogues only): each block also writes, per
+    // solver row, the partial sum of |xin|^2 over its sites to
+    // red[row * red_stride + parity block * nblocks + site block], for a
+    // finishing kernel to sum in block order.
+    double *red;
+    int red_stride;
 };
 
 // Epilogue of a hopping-term launch, per output site x of parity p:
@@ -144,6 +150,13 @@ struct BlasArgs {
 cudaError_t launch_cg_update_xr(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_cg_update_p(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_cg_pq(BlasArgs &B, cudaStream_t s);         // slot (mp): pq, rho, alpha
+// pq, rho, alpha from block partials already in B.partials (B.lat[l].nblocks
+// partials per row of lattice l, row stride B.pstride), e.g. left by a
+// hopping launch with a fused reduction.
+cudaError_t launch_finish_pq(const BlasArgs &B, cudaStream_t s);
+// Row stride of the reduction scratch for lattices of vh sites per parity:
+// enough for the vector kernels and for a hopping launch's block partials.
+int reduce_stride(int vh);
 cudaError_t launch_ru_accumulate(BlasArgs &B, bool force, cudaStream_t s);
 cudaError_t launch_ru_residual(BlasArgs &B, cudaStream_t s);
 cudaError_t launch_init_norms(BlasArgs &B, cudaStream_t s);   // st.b2 = |b|^2, st.tol2 *= |b|^2
@@ -258,8 +271,12 @@ void clover_free(cola_gauge g);
 // Mhat in left in mp; op FULL: D, with D in left in mp).  With st != nullptr
 // rows are filtered by st (filter_ru: only rows with a pending reliable
 // update).
+// With red != null, the last launch of the composition (the one whose xpay
+// input is M in) also leaves the block partials of |M in|^2 in red (row
+// stride red_stride) and, in red_nb[l], the number of partials of each row of
+// lattice l.
 cola_status apply_mdagm_batch(int nlat, const OpLat *L, int prec, int op, int nrhs, CgState *st, bool filter_ru,
-                              cudaStream_t s);
+                              cudaStream_t s, double *red = nullptr, int red_stride = 0, int *red_nb = nullptr);
 cola_status apply_mdagm(cola_gauge g, int prec, int op, void *out, const void *in, void *t, void *mp, int nrhs,
                         CgState *st, bool filter_ru, cudaStream_t s);
 cola_status cuda_check(cudaError_t e, const char *what);

@@ -147,6 +147,7 @@ static TuneEntry tune(int prec, int recon, const DslashArgs &A0, int nparity, bo
             A.rhs_per_thread = nr;
             A.state = nullptr;
             A.filter_ru = 0;
+            A.red = nullptr;
             bool ok = launch_now(prec, recon, A, nparity, dagger, epi, bx, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
             for (int r = 0; r < 3 && ok; ++r) ok = launch_now(prec, recon, A, nparity, dagger, epi, bx, s) == cudaSuccess;

@@ -612,6 +612,45 @@ __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, 
     staged_step<P, RECON, DAGGER, NS, 0>(A, c, cb, in, lo, li, smem_dyn, T, tid, acc, bs);
 }
 
+// |s|^2 of one site, accumulated in the storage real type like the vector
+// kernels' reductions.
+template <typename R>
+__device__ __forceinline__ double site_norm2_d(const Cx<R> (&s)[12]) {
+    R a = R(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a += s[k].re * s[k].re + s[k].im * s[k].im;
+    return (double)a;
+}
+
+// Fused reduction of a hopping launch: the sum of v over the threads of each
+// block row (one right-hand side), in a fixed order, written by the row's
+// first thread to dst_row(threadIdx.y) if write.  Every thread of the block
+// must call it.  Warps that lie within one row (blockDim.x a multiple of 32)
+// reduce by shuffles; other shapes sum the row serially.
+__device__ __forceinline__ void block_row_sum(double v, bool write, double *dst) {
+    __shared__ double sh[256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((blockDim.x & 31) == 0) {
+        v = warp_allsum(v);
+        if ((tid & 31) == 0) sh[tid >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0 && write) {
+            const int wpr = blockDim.x >> 5;
+            double t = 0.0;
+            for (int w = 0; w < wpr; ++w) t += sh[threadIdx.y * wpr + w];
+            *dst = t;
+        }
+    } else {
+        sh[tid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0 && write) {
+            double t = 0.0;
+            for (int i = 0; i < (int)blockDim.x; ++i) t += sh[threadIdx.y * blockDim.x + i];
+            *dst = t;
+        }
+    }
+}
+
 // Grid: x over (site block, right-hand-side group) pairs of every lattice of
 // the batch, group fastest (lattice l owns [block0, block0 + nblocks *
 // ngroups)), so that the blocks reading the same links run back to back and
@@ -622,6 +661,10 @@ __device__ __forceinline__ void hops_staged(const DslashLat &A, const Coord &c, 
 // The staged kernels always run 128-thread blocks.
 #ifndef COLA_STAGED_MINB
 #define COLA_STAGED_MINB 5
+#endif
+// depth of the staged pipeline (hops in flight per thread)
+#ifndef COLA_STAGES
+#define COLA_STAGES 3
 #endif
 template <int P, int NS>
 struct LaunchShape {
@@ -652,6 +695,7 @@ __global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS
     }
     const bool have = cb < g.Vh && live;
     Cx<R> acc[12];
+    double red_v = 0.0;  // |xin|^2 at this site (fused reduction)
     if (have) {
         const Coord c = cb_coord(g, cb, par);
         const char *in = static_cast<const char *>(L.in) + rhs * L.rhs_stride + (1 - par) * L.parity_stride;
@@ -673,6 +717,7 @@ __global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS
             Cx<R> xs[12];
             SpinorIO<P>::load(static_cast<const char *>(L.xin) + rhs * L.rhs_stride + par * L.parity_stride,
                               g.Vh, cb, xs);
+            if (A.red) red_v = site_norm2_d(xs);
             if constexpr (EPI == EPI_CLOVER_X)
                 clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, xs);
 #pragma unroll
@@ -686,6 +731,11 @@ __global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS
     }
     if (have)
         SpinorIO<P>::store(static_cast<char *>(L.out) + rhs * L.rhs_stride + par * L.parity_stride, g.Vh, cb, acc);
+    if constexpr (EPI == EPI_XPAY || EPI == EPI_CLOVER_X) {
+        if (A.red)
+            block_row_sum(red_v, row_ok,
+                          A.red + (size_t)row * A.red_stride + blockIdx.z * L.nblocks + sblk);
+    }
 }
 
 // Multi-right-hand-side variant (direct loads): each thread carries NR
@@ -693,8 +743,11 @@ __global__ void __launch_bounds__(LaunchShape<P, NS>::threads, LaunchShape<P, NS
 // once per NR outputs.  Grid x runs over (site block, right-hand-side group)
 // pairs as in dslash_kernel; a group is blockDim.y x NR right-hand sides.
 template <int P, int RECON, bool DAGGER, int EPI, int NR>
+__device__ __forceinline__ void dslash_mrhs_body(const DslashArgs &A, const DslashLat &L, int cb, int rhs0, int par,
+                                                 const bool (&live)[NR], double (&red_v)[NR]);
+
+template <int P, int RECON, bool DAGGER, int EPI, int NR>
 __global__ void __launch_bounds__(256, 1) dslash_mrhs_kernel(const __grid_constant__ DslashArgs A) {
-    using R = typename Prec<P>::real;
     int l = 0;
     while (l + 1 < A.nlat && (int)blockIdx.x >= A.lat[l + 1].block0) ++l;
     const DslashLat &L = A.lat[l];
@@ -705,13 +758,12 @@ __global__ void __launch_bounds__(256, 1) dslash_mrhs_kernel(const __grid_consta
     const int cb = sblk * blockDim.x + threadIdx.x;
     const int rhs0 = (grp * blockDim.y + threadIdx.y) * NR;
     const int par = A.parity0 + blockIdx.z;
-    if (cb >= g.Vh) return;
     bool live[NR];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const int rhs = rhs0 + k;
-        bool ok = rhs < A.nrhs;
+        bool ok = rhs < A.nrhs && cb < g.Vh;
         if (ok && A.state) {
             const CgState &st = A.state[L.row0 + rhs];
             ok = A.filter_ru ? (st.ru && !st.done) : !st.done;
@@ -719,7 +771,26 @@ __global__ void __launch_bounds__(256, 1) dslash_mrhs_kernel(const __grid_consta
         live[k] = ok;
         any |= ok;
     }
-    if (!any) return;
+    double red_v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) red_v[k] = 0.0;
+    if (any) dslash_mrhs_body<P, RECON, DAGGER, EPI, NR>(A, L, cb, rhs0, par, live, red_v);
+    if constexpr (EPI == EPI_XPAY || EPI == EPI_CLOVER_X) {
+        if (A.red)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                block_row_sum(red_v[k], rhs0 + k < A.nrhs,
+                              A.red + (size_t)(L.row0 + rhs0 + k) * A.red_stride + blockIdx.z * L.nblocks + sblk);
+                __syncthreads();  // the shared sums are reused for the next right-hand side
+            }
+    }
+}
+
+template <int P, int RECON, bool DAGGER, int EPI, int NR>
+__device__ __forceinline__ void dslash_mrhs_body(const DslashArgs &A, const DslashLat &L, int cb, int rhs0, int par,
+                                                 const bool (&live)[NR], double (&red_v)[NR]) {
+    using R = typename Prec<P>::real;
+    const Geom &g = L.g;
     const Coord c = cb_coord(g, cb, par);
     const char *in0 = static_cast<const char *>(L.in) + (size_t)rhs0 * L.rhs_stride + (1 - par) * L.parity_stride;
     const char *lo = static_cast<const char *>(L.links) + par * L.link_parity_stride;
@@ -741,6 +812,7 @@ __global__ void __launch_bounds__(256, 1) dslash_mrhs_kernel(const __grid_consta
             const R a = (R)L.a;
             Cx<R> xs[12];
             SpinorIO<P>::load(static_cast<const char *>(L.xin) + roff, g.Vh, cb, xs);
+            if (A.red) red_v[k] = site_norm2_d(xs);
             if constexpr (EPI == EPI_CLOVER_X)
                 clover_mul<P>(static_cast<const char *>(L.clv) + par * L.clv_parity_stride, g.Vh, cb, xs);
 #pragma unroll
@@ -771,8 +843,8 @@ static inline int staged_depth(int prec) {
         return e ? atoi(e) : -1;
     }();
     if (prec == COLA_F64) return 0;
-    if (env_ns >= 0) return env_ns == 0 ? 0 : 3;
-    return prec == COLA_F16 ? 3 : 0;
+    if (env_ns >= 0) return env_ns == 0 ? 0 : COLA_STAGES;
+    return prec == COLA_F16 ? COLA_STAGES : 0;
 }
 
 template <int P, int RECON, bool DAGGER, int EPI, int NS>
@@ -813,7 +885,7 @@ static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cu
         return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
     } else {
         if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
-        return launch_ns<P, RECON, DAGGER, EPI, 3>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, EPI, COLA_STAGES>(A, nparity, bx, nb, s);
     }
 }
 

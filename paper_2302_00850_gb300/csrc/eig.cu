@@ -24,8 +24,14 @@
 // 12 sweeps with 4 guards, none within 40 without).
 //
 // FP64 throughout: packed fields, the FP64 normal operator, reductions in
-// fixed order (block partials, one finishing block per result).  The host
-// drives the sweep and reads the few scalars of each step.
+// fixed order (block partials, one finishing block per result).  The
+// minimisation of each vector runs on the device: its scalars (the rotation
+// of the line search, beta, the projection coefficients, the stopping test)
+// are computed by one-thread control kernels into device memory, the linear
+// combinations read their coefficients from there, and the CG loop is a
+// while node of a CUDA graph (one graph per vector index, built on first use
+// in a call).  The host launches the graphs of a sweep back to back, runs the
+// Rayleigh-Ritz step, and reads the residuals once per sweep.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -74,30 +80,56 @@ struct DotArgs {
     int nb;
 };
 
-__global__ void __launch_bounds__(kBlk) dots_kernel(const __grid_constant__ DotArgs A) {
-    __shared__ double sh[kBlk / 32];
+// Pairs are taken four at a time with one block reduction per group, and a
+// field shared by consecutive pairs (the basis dots <v_i, g> all read g) is
+// loaded once.  The reduction order per pair is the same fixed order as
+// block_sum: warp butterflies, then the warps in order.
+constexpr int kDotGroup = 4;
+
+__global__ void __launch_bounds__(kBlk, 2) dots_kernel(const __grid_constant__ DotArgs A) {
+    __shared__ double sh[kBlk / 32][2 * kDotGroup];
     int par, cb;
     const bool ok = site(A.F, par, cb);
-    for (int k = 0; k < A.n; ++k) {
-        double re = 0.0, im = 0.0;
-        if (ok) {
-            Cx<double> x[12], y[12];
-            SpinorIO<COLA_F64>::load(at(A.a[k], A.F.vh, par), A.F.vh, cb, x);
-            SpinorIO<COLA_F64>::load(at(A.b[k], A.F.vh, par), A.F.vh, cb, y);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const char *pa = nullptr, *pb = nullptr;
+    Cx<double> x[12], y[12];
+    for (int k0 = 0; k0 < A.n; k0 += kDotGroup) {
+        double v[2 * kDotGroup];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                re = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, re));
-                im = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, im));
+        for (int q = 0; q < kDotGroup; ++q) {
+            const int k = k0 + q;
+            double re = 0.0, im = 0.0;
+            if (ok && k < A.n) {
+                if (A.a[k] != pa) {
+                    pa = A.a[k];
+                    SpinorIO<COLA_F64>::load(at(pa, A.F.vh, par), A.F.vh, cb, x);
+                }
+                if (A.b[k] != pb) {
+                    pb = A.b[k];
+                    SpinorIO<COLA_F64>::load(at(pb, A.F.vh, par), A.F.vh, cb, y);
+                }
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    re = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, re));
+                    im = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, im));
+                }
             }
+            v[2 * q] = re;
+            v[2 * q + 1] = im;
         }
-        const double tr = block_sum(re, sh);
+#pragma unroll
+        for (int q = 0; q < 2 * kDotGroup; ++q) v[q] = warp_allsum(v[q]);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 2 * kDotGroup; ++q) sh[warp][q] = v[q];
         __syncthreads();
-        const double ti = block_sum(im, sh);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            A.partials[((size_t)k * A.nb + blockIdx.x) * 2] = tr;
-            A.partials[((size_t)k * A.nb + blockIdx.x) * 2 + 1] = ti;
+        if (threadIdx.x < 2 * kDotGroup) {
+            const int k = k0 + (int)threadIdx.x / 2;
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][threadIdx.x];
+            if (k < A.n) A.partials[((size_t)k * A.nb + blockIdx.x) * 2 + (threadIdx.x & 1)] = t;
         }
+        __syncthreads();
     }
 }
 
@@ -139,6 +171,145 @@ __global__ void __launch_bounds__(kBlk) lincomb_kernel(const __grid_constant__ C
         for (int c = 0; c < 12; ++c) cmac(acc[c], w, x[c]);
     }
     SpinorIO<COLA_F64>::store(const_cast<char *>(at(A.out, A.F.vh, par)), A.F.vh, cb, acc);
+}
+
+// ------------------------------------------------------ device control --
+// Coefficient sets of the linear combinations of one minimisation.
+enum CoefSet { C_PROJ = 0, C_NORM, C_GRAD, C_PERP, C_ROT, C_DIR, kCoefSets };
+
+// Scalars of the minimisation of one vector, on the device.
+struct EigDev {
+    double mu, gg, gg0, gg_new, pn, pn2, beta;
+    double2 xpn;
+    int k, stop, halt, cont, status, steps;
+    double2 coef[kCoefSets][kMaxTerms];
+};
+
+// out = sum_k coef[k] in_k with coefficients read from device memory; skipped
+// when the minimisation has halted (mask bit 0) or its loop has stopped
+// (mask bit 1).
+struct CombDevArgs {
+    Fields F;
+    int n;
+    char *out;
+    const char *in[kMaxTerms];
+    const EigDev *e;
+    int set;
+    int mask;
+};
+
+__global__ void __launch_bounds__(kBlk) lincomb_dev_kernel(const __grid_constant__ CombDevArgs A) {
+    if (((A.mask & 1) && A.e->halt) || ((A.mask & 2) && A.e->stop)) return;
+    int par, cb;
+    if (!site(A.F, par, cb)) return;
+    Cx<double> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = {0.0, 0.0};
+    for (int k = 0; k < A.n; ++k) {
+        Cx<double> x[12];
+        SpinorIO<COLA_F64>::load(at(A.in[k], A.F.vh, par), A.F.vh, cb, x);
+        const double2 cw = A.e->coef[A.set][k];
+        const Cx<double> w = {cw.x, cw.y};
+#pragma unroll
+        for (int c = 0; c < 12; ++c) cmac(acc[c], w, x[c]);
+    }
+    SpinorIO<COLA_F64>::store(const_cast<char *>(at(A.out, A.F.vh, par)), A.F.vh, cb, acc);
+}
+
+enum CtlStep { CTL_PROJ, CTL_NORM, CTL_MU, CTL_GRAD0, CTL_LOOP0, CTL_PERP, CTL_ROT, CTL_GRAD, CTL_END };
+
+struct CtlParams {
+    int j;          // vector index: number of earlier vectors projected out
+    int max_cg;
+    double gamma, tol;
+};
+
+__device__ __forceinline__ bool keep_going(const EigDev &e, const CtlParams &p) {
+    return !(e.gg <= p.gamma * p.gamma * e.gg0 || sqrt(e.gg) <= 0.1 * p.tol * fabs(e.mu) || e.gg == 0.0) &&
+           e.k < p.max_cg;
+}
+
+// The gradient's norm after projecting out v_0 .. v_{j-1}: the dots are
+// {<v_i, g>} (i < j), |g|^2, then optionally <x, p>.
+__device__ __forceinline__ void gradient_norm(EigDev &e, const double2 *d, int j) {
+    double n2 = d[j].x;
+    e.coef[C_PROJ][0] = make_double2(1.0, 0.0);
+    for (int i = 0; i < j; ++i) {
+        e.coef[C_PROJ][1 + i] = make_double2(-d[i].x, -d[i].y);
+        n2 -= d[i].x * d[i].x + d[i].y * d[i].y;
+    }
+    e.gg_new = fmax(n2, 0.0);
+}
+
+// One-thread control steps; d holds the latest finished dot products.
+template <int STEP>
+__global__ void eig_ctl_kernel(EigDev *ep, const double2 *d, const CtlParams p, cudaGraphConditionalHandle h) {
+    EigDev &e = *ep;
+    if constexpr (STEP == CTL_PROJ) {  // x -= sum_i <v_i, x> v_i
+        e.coef[C_PROJ][0] = make_double2(1.0, 0.0);
+        for (int i = 0; i < p.j; ++i) e.coef[C_PROJ][1 + i] = make_double2(-d[i].x, -d[i].y);
+    } else if constexpr (STEP == CTL_NORM) {  // x /= |x|
+        if (e.halt) return;
+        if (!(d[0].x > 0.0) || !isfinite(d[0].x)) {
+            e.halt = 1;
+            e.status = COLA_ERR_BREAKDOWN;
+            return;
+        }
+        e.coef[C_NORM][0] = make_double2(1.0 / sqrt(d[0].x), 0.0);
+    } else if constexpr (STEP == CTL_MU) {  // mu = <x, A x>;  g = y - mu x
+        e.mu = d[0].x;
+        e.coef[C_GRAD][0] = make_double2(1.0, 0.0);
+        e.coef[C_GRAD][1] = make_double2(-e.mu, 0.0);
+    } else if constexpr (STEP == CTL_GRAD0) {
+        gradient_norm(e, d, p.j);
+        e.gg = e.gg0 = e.gg_new;
+    } else if constexpr (STEP == CTL_LOOP0) {
+        e.k = 0;
+        e.stop = 0;
+        e.cont = !e.halt && keep_going(e, p);
+        cudaGraphSetConditional(h, e.cont ? 1u : 0u);
+    } else if constexpr (STEP == CTL_PERP) {  // p -= <x, p> x; |p|
+        const double2 xp = d[0];
+        e.pn2 = d[1].x - (xp.x * xp.x + xp.y * xp.y);
+        if (!(e.pn2 > 0.0)) {
+            e.stop = 1;
+            return;
+        }
+        e.pn = sqrt(e.pn2);
+        e.coef[C_PERP][0] = make_double2(1.0, 0.0);
+        e.coef[C_PERP][1] = make_double2(-xp.x, -xp.y);
+    } else if constexpr (STEP == CTL_ROT) {  // exact line search on span(x, p^): d = {<x, z>, <p, z>}
+        if (e.stop) return;
+        const double a = e.mu, b = d[0].x / e.pn, cc = d[1].x / e.pn2;
+        const double hh = 0.5 * (a - cc), R = sqrt(hh * hh + b * b);
+        if (!(R > 0.0)) {
+            e.stop = 1;
+            return;
+        }
+        // cos 2t = -h / R, sin 2t = -b / R; half angle with cos t >= 0
+        const double c2 = -hh / R, s2 = -b / R;
+        const double ct = sqrt(fmax(0.0, 0.5 * (1.0 + c2)));
+        const double st = ct > 1e-8 ? s2 / (2.0 * ct) : (s2 >= 0.0 ? 1.0 : -1.0) * sqrt(fmax(0.0, 0.5 * (1.0 - c2)));
+        e.coef[C_ROT][0] = make_double2(ct, 0.0);
+        e.coef[C_ROT][1] = make_double2(st / e.pn, 0.0);
+        e.mu = 0.5 * (a + cc) - R;
+        e.coef[C_GRAD][0] = make_double2(1.0, 0.0);
+        e.coef[C_GRAD][1] = make_double2(-e.mu, 0.0);
+    } else if constexpr (STEP == CTL_GRAD) {  // d = {<v_i, g'>}, |g'|^2, <x', p>;  p = g' + beta (p - <x', p> x')
+        if (e.stop) return;
+        gradient_norm(e, d, p.j);
+        e.xpn = d[p.j + 1];
+        e.beta = e.gg_new / e.gg;
+        e.coef[C_DIR][0] = make_double2(1.0, 0.0);
+        e.coef[C_DIR][1] = make_double2(e.beta, 0.0);
+        e.coef[C_DIR][2] = make_double2(-e.beta * e.xpn.x, -e.beta * e.xpn.y);
+    } else {  // CTL_END
+        ++e.steps;  // operator applications of the loop (one per pass)
+        if (!e.stop) e.gg = e.gg_new;
+        e.k += 1;
+        e.cont = !e.stop && !e.halt && keep_going(e, p);
+        cudaGraphSetConditional(h, e.cont ? 1u : 0u);
+    }
 }
 
 // Eigen-decomposition of the Hermitian n x n matrix H (row-major, destroyed)
@@ -254,8 +425,14 @@ struct Ctx {
     double2 *H, *Ud;   // N x N
     double *wd;
     int *sweeps;
+    EigDev *e;         // scalars of the current minimisation
     cudaStream_t s;
     long applications = 0;
+    std::vector<cudaGraphExec_t> ritz;  // one minimisation graph per vector index, built on first use
+    ~Ctx() {
+        for (cudaGraphExec_t x : ritz)
+            if (x) cudaGraphExecDestroy(x);
+    }
 };
 
 cola_status apply_a(Ctx &c, char *out, const char *in) {
@@ -330,73 +507,180 @@ cola_status normalize(Ctx &c, char *x) {
     return comb(c, x, {{x, cplx(1.0 / std::sqrt(d[0].x))}});
 }
 
-// Ritz-functional CG for v_j over the complement of v_0 .. v_{j-1}.  Three
-// host reads per step: {<x, p>, |p|^2}, {<x, A p>, <p, A p>} and
-// {<v_i, g> (i < j), |g|^2, <x, p>}; the norms after a projection follow from
-// those (|p - <x,p> x|^2 = |p|^2 - |<x,p>|^2 for unit x, and likewise for g).
-cola_status ritz_cg(Ctx &c, int j, int max_cg, double gamma, double tol) {
-    char *x = c.V[j], *y = c.x_y, *g = c.g_, *p = c.p, *z = c.z;
-    EIG_TRY(project(c, x, j));
-    EIG_TRY(normalize(c, x));
-    EIG_TRY(apply_a(c, y, x));
-    std::vector<double2> d;
-    EIG_TRY(dots(c, {{x, y}}, d));
-    double mu = d[0].x;
-    // g = Q (y - mu x), one classical Gram-Schmidt pass
-    auto gradient = [&](double &gg, double2 *xp) -> cola_status {
-        EIG_TRY(comb(c, g, {{y, cplx(1.0)}, {x, cplx(-mu)}}));
-        std::vector<std::pair<const char *, const char *>> ab;
-        for (int i = 0; i < j; ++i) ab.push_back({c.V[i], g});
-        ab.push_back({g, g});
-        if (xp) ab.push_back({x, p});
-        EIG_TRY(dots(c, ab, d));
-        double n2 = d[j].x;
-        if (j > 0) {
-            std::vector<std::pair<const char *, double2>> t = {{g, cplx(1.0)}};
-            for (int i = 0; i < j; ++i) {
-                t.push_back({c.V[i], cplx(-d[i].x, -d[i].y)});
-                n2 -= d[i].x * d[i].x + d[i].y * d[i].y;
-            }
-            EIG_TRY(comb(c, g, t));
-        }
-        gg = std::max(n2, 0.0);
-        if (xp) *xp = d[j + 1];
-        return COLA_OK;
-    };
-    double gg0 = 0.0;
-    EIG_TRY(gradient(gg0, nullptr));
-    double gg = gg0;
-    EIG_CUDA(cudaMemcpyAsync(p, g, c.fb, cudaMemcpyDeviceToDevice, c.s), "p = g");
-    for (int k = 0; k < max_cg; ++k) {
-        if (gg <= gamma * gamma * gg0 || std::sqrt(gg) <= 0.1 * tol * std::fabs(mu) || gg == 0.0) break;
-        // p <- p - <x, p> x (keep p orthogonal to x)
-        EIG_TRY(dots(c, {{x, p}, {p, p}}, d));
-        const double2 xp = d[0];
-        const double pn2 = d[1].x - (xp.x * xp.x + xp.y * xp.y);
-        if (!(pn2 > 0.0)) break;
-        EIG_TRY(comb(c, p, {{p, cplx(1.0)}, {x, cplx(-xp.x, -xp.y)}}));
-        const double pn = std::sqrt(pn2);
-        EIG_TRY(apply_a(c, z, p));  // z = A p = pn A p^
-        EIG_TRY(dots(c, {{x, z}, {p, z}}, d));
-        const double a = mu, b = d[0].x / pn, cc = d[1].x / pn2;
-        const double h = 0.5 * (a - cc), R = std::sqrt(h * h + b * b);
-        if (!(R > 0.0)) break;
-        // cos 2t = -h / R, sin 2t = -b / R; half angle with cos t >= 0
-        const double c2 = -h / R, s2 = -b / R;
-        const double ct = std::sqrt(std::max(0.0, 0.5 * (1.0 + c2)));
-        const double st = ct > 1e-8 ? s2 / (2.0 * ct) : (s2 >= 0.0 ? 1.0 : -1.0) * std::sqrt(std::max(0.0, 0.5 * (1.0 - c2)));
-        EIG_TRY(comb(c, x, {{x, cplx(ct)}, {p, cplx(st / pn)}}));
-        EIG_TRY(comb(c, y, {{y, cplx(ct)}, {z, cplx(st / pn)}}));
-        mu = 0.5 * (a + cc) - R;
-        double gg_new = 0.0;
-        double2 xpn;
-        EIG_TRY(gradient(gg_new, &xpn));  // also <x', p>
-        const double beta = gg_new / gg;
-        // p = g' + beta (p - <x', p> x')
-        EIG_TRY(comb(c, p, {{g, cplx(1.0)}, {p, cplx(beta)}, {x, cplx(-beta * xpn.x, -beta * xpn.y)}}));
-        gg = gg_new;
+// ------------------------------------------------ device-driven minimisation --
+// Launches on stream st (capturing or not) with results left on the device.
+void dots_dev(Ctx &c, cudaStream_t st, const std::vector<std::pair<const char *, const char *>> &ab) {
+    DotArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.F = c.F;
+    A.n = (int)ab.size();
+    for (int k = 0; k < A.n; ++k) {
+        A.a[k] = ab[k].first;
+        A.b[k] = ab[k].second;
     }
-    return normalize(c, x);
+    A.partials = c.partials;
+    A.nb = c.nb;
+    dots_kernel<<<c.nb, kBlk, 0, st>>>(A);
+    dots_finish_kernel<<<A.n, kBlk, 0, st>>>(c.partials, c.nb, c.dres);
+}
+
+void comb_dev(Ctx &c, cudaStream_t st, char *out, const std::vector<const char *> &in, int set, int mask) {
+    CombDevArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.F = c.F;
+    A.n = (int)in.size();
+    A.out = out;
+    for (int k = 0; k < A.n; ++k) A.in[k] = in[k];
+    A.e = c.e;
+    A.set = set;
+    A.mask = mask;
+    lincomb_dev_kernel<<<c.nb, kBlk, 0, st>>>(A);
+}
+
+template <int STEP>
+void ctl(Ctx &c, cudaStream_t st, const CtlParams &p, cudaGraphConditionalHandle h = 0) {
+    eig_ctl_kernel<STEP><<<1, 1, 0, st>>>(c.e, c.dres, p, h);
+}
+
+// {<v_i, f>} for i < j, then |f|^2, then the extra pairs
+std::vector<std::pair<const char *, const char *>> against_basis(Ctx &c, int j, const char *f) {
+    std::vector<std::pair<const char *, const char *>> ab;
+    for (int i = 0; i < j; ++i) ab.push_back({c.V[i], f});
+    ab.push_back({f, f});
+    return ab;
+}
+
+std::vector<const char *> with_basis(Ctx &c, int j, const char *f) {
+    std::vector<const char *> in = {f};
+    for (int i = 0; i < j; ++i) in.push_back(c.V[i]);
+    return in;
+}
+
+// The minimisation of v_j as one graph: project v_j on the complement of
+// v_0 .. v_{j-1} (classical Gram-Schmidt, twice), normalise, y = A x, the
+// projected gradient g = Q (y - mu x), p = g, then while the gradient has not
+// fallen by gamma (and fewer than max_cg steps ran): p <- p - <x, p> x,
+// z = A p, the exact line search on span(x, p^), x and y rotated, the new
+// projected gradient, p = g' + beta (p - <x', p> x'); finally v_j is
+// normalised again.  Every scalar stays on the device (EigDev).
+cola_status build_ritz_graph(Ctx &c, int j, const CtlParams &p, cudaGraphExec_t *out) {
+    char *x = c.V[j], *y = c.x_y, *g = c.g_, *pp = c.p, *z = c.z;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cola_status st = COLA_OK;
+    auto fail = [&](cola_status e) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        return e;
+    };
+    if ((st = cuda_check(cudaGraphCreate(&graph, 0), "graph create")) != COLA_OK) return fail(st);
+    cudaGraphConditionalHandle h;
+    if ((st = cuda_check(cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault),
+                         "graph conditional")) != COLA_OK)
+        return fail(st);
+    if ((st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream")) != COLA_OK)
+        return fail(st);
+    if ((st = cuda_check(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                         "capture")) != COLA_OK)
+        return fail(st);
+    // prologue
+    for (int rep = 0; rep < 2 && j > 0; ++rep) {
+        std::vector<std::pair<const char *, const char *>> ab;
+        for (int i = 0; i < j; ++i) ab.push_back({c.V[i], x});
+        dots_dev(c, cs, ab);
+        ctl<CTL_PROJ>(c, cs, p);
+        comb_dev(c, cs, x, with_basis(c, j, x), C_PROJ, 1);
+    }
+    dots_dev(c, cs, {{x, x}});
+    ctl<CTL_NORM>(c, cs, p);
+    comb_dev(c, cs, x, {x}, C_NORM, 1);
+    st = apply_mdagm(c.g, COLA_F64, c.op, y, x, c.t, c.mp, 1, nullptr, false, cs);
+    if (st == COLA_OK) {
+        dots_dev(c, cs, {{x, y}});
+        ctl<CTL_MU>(c, cs, p);
+        comb_dev(c, cs, g, {y, x}, C_GRAD, 1);
+        dots_dev(c, cs, against_basis(c, j, g));
+        ctl<CTL_GRAD0>(c, cs, p);
+        if (j > 0) comb_dev(c, cs, g, with_basis(c, j, g), C_PROJ, 1);
+        st = cuda_check(cudaMemcpyAsync(pp, g, c.fb, cudaMemcpyDeviceToDevice, cs), "p = g");
+    }
+    if (st == COLA_OK) {
+        ctl<CTL_LOOP0>(c, cs, p, h);
+        st = cuda_check(cudaGetLastError(), "eigensolver prologue");
+    }
+    // the loop as a while node after the prologue
+    cudaGraph_t body = nullptr;
+    if (st == COLA_OK) {
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edata = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t capg;
+        st = cuda_check(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, &edata, &ndeps), "capture info");
+        if (st == COLA_OK) {
+            cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+            wp.conditional.handle = h;
+            wp.conditional.type = cudaGraphCondTypeWhile;
+            wp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            st = cuda_check(cudaGraphAddNode(&wnode, capg, deps, edata, ndeps, &wp), "graph while node");
+            if (st == COLA_OK) {
+                body = wp.conditional.phGraph_out[0];
+                st = cuda_check(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1,
+                                                                    cudaStreamSetCaptureDependencies),
+                                "capture dependencies");
+            }
+        }
+    }
+    // epilogue: normalise v_j
+    if (st == COLA_OK) {
+        dots_dev(c, cs, {{x, x}});
+        ctl<CTL_NORM>(c, cs, p);
+        comb_dev(c, cs, x, {x}, C_NORM, 1);
+        st = cuda_check(cudaGetLastError(), "eigensolver epilogue");
+    }
+    {
+        cudaGraph_t g_out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g_out);
+        if (st == COLA_OK) st = cuda_check(e, "end capture");
+    }
+    if (st != COLA_OK) return fail(st);
+    // the loop body
+    if ((st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                         "capture")) != COLA_OK)
+        return fail(st);
+    dots_dev(c, cs, {{x, pp}, {pp, pp}});
+    ctl<CTL_PERP>(c, cs, p);
+    comb_dev(c, cs, pp, {pp, x}, C_PERP, 3);
+    st = apply_mdagm(c.g, COLA_F64, c.op, z, pp, c.t, c.mp, 1, nullptr, false, cs);  // z = A p = pn A p^
+    if (st == COLA_OK) {
+        dots_dev(c, cs, {{x, z}, {pp, z}});
+        ctl<CTL_ROT>(c, cs, p);
+        comb_dev(c, cs, x, {x, pp}, C_ROT, 3);
+        comb_dev(c, cs, y, {y, z}, C_ROT, 3);
+        comb_dev(c, cs, g, {y, x}, C_GRAD, 3);
+        std::vector<std::pair<const char *, const char *>> ab = against_basis(c, j, g);
+        ab.push_back({x, pp});
+        dots_dev(c, cs, ab);
+        ctl<CTL_GRAD>(c, cs, p);
+        if (j > 0) comb_dev(c, cs, g, with_basis(c, j, g), C_PROJ, 3);
+        comb_dev(c, cs, pp, {g, pp, x}, C_DIR, 3);
+        ctl<CTL_END>(c, cs, p, h);
+        st = cuda_check(cudaGetLastError(), "eigensolver step");
+    }
+    {
+        cudaGraph_t g_out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g_out);
+        if (st == COLA_OK) st = cuda_check(e, "end capture");
+    }
+    if (st != COLA_OK) return fail(st);
+    if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate")) != COLA_OK) return fail(st);
+    *out = exec;
+    exec = nullptr;
+    fail(COLA_OK);  // the graph and the capture stream are no longer needed
+    return COLA_OK;
 }
 
 cola_status arg_error(const std::string &m) {
@@ -442,7 +726,8 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
     const size_t o_u = o_h + al((size_t)N * N * sizeof(double2));
     const size_t o_w = o_u + al((size_t)N * N * sizeof(double2));
     const size_t o_sw = o_w + al(N * sizeof(double));
-    const size_t total = o_sw + 256;
+    const size_t o_e = o_sw + 256;
+    const size_t total = o_e + al(sizeof(EigDev));
     void *ws = nullptr;
     EIG_TRY(ws_slot(g, cola_gauge_s::kSlotMultishift, total, &ws));  // shares the multi-shift block
     char *w = static_cast<char *>(ws);
@@ -464,6 +749,8 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
     c.Ud = reinterpret_cast<double2 *>(w + o_u);
     c.wd = reinterpret_cast<double *>(w + o_w);
     c.sweeps = reinterpret_cast<int *>(w + o_sw);
+    c.e = reinterpret_cast<EigDev *>(w + o_e);
+    c.ritz.assign(N, nullptr);
 
     const size_t canon = (size_t)G.V * 12 * 16;
     const int pmask = c.F.nparity == 1 ? 1 : 3;
@@ -483,10 +770,23 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
         EIG_TRY(normalize(c, c.V[i]));
     }
     std::vector<double> lam(N, 0.0), res(N, 0.0);
+    EIG_CUDA(cudaMemsetAsync(c.e, 0, sizeof(EigDev), s), "eigensolver state");
+    {
+        // the operator's launch shape is tuned outside the graph captures
+        TuneOnlyScope tune_only;
+        EIG_TRY(apply_mdagm(g, COLA_F64, c.op, c.z, c.V[0], c.t, c.mp, 1, nullptr, false, s));
+    }
     int sweep = 0;
     bool converged = false;
     for (; sweep < prm->max_sweeps && !converged; ++sweep) {
-        for (int j = 0; j < N; ++j) EIG_TRY(ritz_cg(c, j, prm->max_cg, prm->gamma, prm->tol));
+        for (int j = 0; j < N; ++j) {
+            if (!c.ritz[j]) {
+                const CtlParams cp = {j, prm->max_cg, prm->gamma, prm->tol};
+                EIG_TRY(build_ritz_graph(c, j, cp, &c.ritz[j]));
+            }
+            EIG_CUDA(cudaGraphLaunch(c.ritz[j], s), "eigensolver minimisation");
+            ++c.applications;  // y = A x of the prologue; the loop's are counted on the device
+        }
         // Rayleigh-Ritz on span(V)
         for (int i = 0; i < N; ++i) EIG_TRY(apply_a(c, c.W[i], c.V[i]));
         std::vector<std::pair<const char *, const char *>> ab;
@@ -507,13 +807,15 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
         EIG_CUDA(cudaMemcpyAsync(U.data(), c.Ud, N * N * sizeof(double2), cudaMemcpyDeviceToHost, s), "U readback");
         EIG_CUDA(cudaMemcpyAsync(lam.data(), c.wd, N * sizeof(double), cudaMemcpyDeviceToHost, s), "lambda readback");
         EIG_CUDA(cudaStreamSynchronize(s), "Rayleigh-Ritz");
-        // V <- V U, W <- W U (through T, then swap)
+        // V <- V U, W <- W U through T (V is copied back: the minimisation
+        // graphs hold the addresses of the V buffers; W swaps)
         for (int j = 0; j < N; ++j) {
             std::vector<std::pair<const char *, double2>> t;
             for (int i = 0; i < N; ++i) t.push_back({c.V[i], U[i * N + j]});
             EIG_TRY(comb(c, c.T[j], t));
         }
-        std::swap(c.V, c.T);
+        for (int j = 0; j < N; ++j)
+            EIG_CUDA(cudaMemcpyAsync(c.V[j], c.T[j], c.fb, cudaMemcpyDeviceToDevice, s), "V = V U");
         for (int j = 0; j < N; ++j) {
             std::vector<std::pair<const char *, double2>> t;
             for (int i = 0; i < N; ++i) t.push_back({c.W[i], U[i * N + j]});
@@ -525,11 +827,24 @@ extern "C" cola_status cola_eig_lowest(cola_gauge g, void *evecs_dev, double *ev
         ab.clear();
         for (int j = 0; j < N; ++j) ab.push_back({c.T[j], c.T[j]});
         EIG_TRY(dots(c, ab, h));
+        EigDev he;
+        EIG_CUDA(cudaMemcpyAsync(&he, c.e, sizeof(EigDev), cudaMemcpyDeviceToHost, s), "eigensolver state");
+        EIG_CUDA(cudaStreamSynchronize(s), "eigensolver state");
+        if (he.status != COLA_OK) {
+            set_error("eigensolver: a vector vanished after orthogonalisation (dependent initial vectors?)");
+            return (cola_status)he.status;
+        }
         converged = true;
         for (int j = 0; j < N; ++j) {
             res[j] = std::sqrt(std::max(0.0, h[j].x));
             if (j < prm->nev) converged &= res[j] <= prm->tol * std::fabs(lam[j]);
         }
+    }
+    {
+        EigDev he;
+        EIG_CUDA(cudaMemcpyAsync(&he, c.e, sizeof(EigDev), cudaMemcpyDeviceToHost, s), "eigensolver state");
+        EIG_CUDA(cudaStreamSynchronize(s), "eigensolver state");
+        c.applications += he.steps;
     }
     for (int i = 0; i < N; ++i) {
         char *dst = static_cast<char *>(evecs_dev) + i * canon;

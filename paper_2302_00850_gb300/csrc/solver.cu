@@ -74,6 +74,8 @@ struct SolveCtx {
     LatCtx lat[kMaxBatch];
     cola_gauge owner;  // holds states and reduction scratch
     int prec, xprec, op, nrhs, nparity;
+    int fuse_pq;       // <p, Ap> from the operator's last hopping launch (no shifted rows)
+    int red_stride;    // row stride of the reduction scratch
 };
 
 enum VecId { V_T, V_MP, V_P, V_Q, V_RLO, V_XLO, V_B, V_XHI, V_RHI, V_AX, V_T64, V_MP64, V_BORIG };
@@ -118,11 +120,11 @@ BlasArgs blas(const SolveCtx &c, std::initializer_list<std::pair<VecId, int>> id
 }
 
 cola_status mdagm(const SolveCtx &c, int prec, VecId out, VecId in, VecId t, VecId mp, CgState *st, bool filter_ru,
-                  cudaStream_t s) {
+                  cudaStream_t s, double *red = nullptr, int *red_nb = nullptr) {
     OpLat L[kMaxBatch];
     for (int l = 0; l < c.nlat; ++l)
         L[l] = {c.lat[l].g, vec(c.lat[l], out), vec(c.lat[l], in), vec(c.lat[l], t), vec(c.lat[l], mp), c.lat[l].row0};
-    return apply_mdagm_batch(c.nlat, L, prec, c.op, c.nrhs, st, filter_ru, s);
+    return apply_mdagm_batch(c.nlat, L, prec, c.op, c.nrhs, st, filter_ru, s, red, c.red_stride, red_nb);
 }
 
 cola_status ru_block(const SolveCtx &c, cudaStream_t s) {
@@ -136,9 +138,19 @@ cola_status ru_block(const SolveCtx &c, cudaStream_t s) {
 }
 
 cola_status iter_head(const SolveCtx &c, cudaStream_t s) {
-    COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, s));
     BlasArgs P = blas(c, {{V_MP, c.prec}, {V_P, c.prec}});  // <p, A p> = |M p|^2 (+ sigma |p|^2), alpha
-    COLA_CUDA(launch_cg_pq(P, s), "cg <p, Ap>");
+    if (c.fuse_pq) {
+        // the operator's last hopping launch reads M p as its xpay input and
+        // leaves the block partials of |M p|^2; the finishing kernel sums them
+        int nb[kMaxBatch];
+        COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, s, c.owner->partials, nb));
+        for (int l = 0; l < c.nlat; ++l) P.lat[l].nblocks = nb[l];
+        P.pstride = c.red_stride;
+        COLA_CUDA(launch_finish_pq(P, s), "cg <p, Ap>");
+    } else {
+        COLA_TRY(mdagm(c, c.prec, V_Q, V_P, V_T, V_MP, c.owner->states, false, s));
+        COLA_CUDA(launch_cg_pq(P, s), "cg <p, Ap>");
+    }
     BlasArgs B = blas(c, {{V_XLO, c.xprec}, {V_RLO, c.prec}, {V_P, c.prec}, {V_Q, c.prec}});
     COLA_CUDA(launch_cg_update_xr(B, s), "cg update x, r");
     return COLA_OK;
@@ -394,9 +406,11 @@ cola_status solve_batch_pass(int nlat, const cola_gauge *gs, void *const *xs, co
         COLA_TRY(ws_slot(g, S_MP64, hi, &L.mp64));
         L.borig = nullptr;
         if (dirac) COLA_TRY(ws_slot(g, S_BORIG, hi, &L.borig));
-        maxblocks = std::max(maxblocks, (G.Vh * 2 + 255) / 256);  // vector kernels: 256 sites per block
+        maxblocks = std::max(maxblocks, reduce_stride(G.Vh));
     }
     COLA_TRY(ws_reduce(c.owner, nrows, maxblocks));
+    c.red_stride = maxblocks;
+    c.fuse_pq = shifts == nullptr;
     COLA_TRY(ws_states(c.owner, nrows));
     CgState *hs = c.owner->h_states;
 
