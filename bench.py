@@ -1078,7 +1078,10 @@ def eig_measurements(cola, dev):
 
 
 def run_dslash_only(args):
-    """Chained parity Dslash applies only (the case profiled with ncu)."""
+    """Chained parity Dslash applies only (the case profiled with ncu): the
+    32^3x64 workload, or with --clover the clover normal operator on
+    --lattice, or with --nrhs > 1 that many point sources of 24^3x48 in one
+    multi-right-hand-side launch."""
     import torch
 
     import paper_2302_00850_gb300 as cola
@@ -1094,6 +1097,14 @@ def run_dslash_only(args):
         dev = torch.device("cuda", 0)
         u = synth.gauge_field(dims, EPS, synth.seed_for(CONFIG_ID, 0), device=dev, as_numpy=False)
         b = torch.from_numpy(synth.gaussian_spinor(dims, synth.seed_for(CONFIG_ID, 1))).to(dev)
+    elif args.nrhs > 1:
+        import synth
+
+        # the 12 point sources of the multi-RHS workload (24^3x48, kappa 0.124, links exp(0.3 i H))
+        dims = (24, 24, 24, 48)
+        dev = torch.device("cuda", 0)
+        u = synth.gauge_field(dims, 0.3, synth.seed_for(3, 0), device=dev, as_numpy=False)
+        b = torch.from_numpy(synth.point_sources(dims)[:args.nrhs]).to(dev)
     else:
         u, b = make_inputs(torch.device("cuda", 0))
     prec = args.prec
@@ -1102,19 +1113,20 @@ def run_dslash_only(args):
         g = cola.Gauge(u, dims, KAPPA, BC, precisions=("f64", prec), recon={"f64": 18, prec: args.recon})
         g.attach_clover(CSW)
     else:
-        g = cola.Gauge(u, DIMS, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
+        g = cola.Gauge(u, dims, KAPPA, BC, precisions=(prec,), recon={prec: args.recon})
     del u
+    nrhs = max(args.nrhs, 1)
     p = cola.pack(g, b, prec)
-    t = g.empty_packed(prec)
+    t = g.empty_packed(prec, nrhs)
     for _ in range(args.reps):
         if args.clover:
             cola.mdagm(g, t, p, op="eo", prec=prec)
         else:
-            cola.dslash(g, t, p, parity=1, prec=prec)
-            cola.dslash(g, p, t, parity=0, prec=prec)
+            cola.dslash(g, t, p, parity=1, prec=prec, nrhs=nrhs)
+            cola.dslash(g, p, t, parity=0, prec=prec, nrhs=nrhs)
     torch.cuda.synchronize()
     print(json.dumps({"dslash_only": prec, "recon": args.recon, "reps": args.reps, "clover": bool(args.clover),
-                      "lattice": "x".join(map(str, dims))}))
+                      "nrhs": nrhs, "lattice": "x".join(map(str, dims))}))
 
 
 def run_gauge_only(args):
@@ -1175,6 +1187,8 @@ def main():
     ap.add_argument("--clover", action="store_true",
                     help="with --dslash-only: the clover normal operator; with --gauge-only: also the clover force")
     ap.add_argument("--recon", type=int, default=12)
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="with --dslash-only: that many of the 12 point sources of 24^3x48 per launch")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

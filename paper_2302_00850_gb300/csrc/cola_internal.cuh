@@ -561,19 +561,33 @@ __device__ __forceinline__ void herm6_mul(const R (&m)[kCloverReals], const Cx<R
         }
 }
 
-// v <- C v for the clover field C (A or A^-1) of one parity at site cb.
+// v <- C v for the clover field C (A or A^-1) of one parity at site cb, v in
+// the packed spin basis (v' = S v, S = (gamma_t + gamma5) / sqrt(2)).  The
+// chirality blocks act on the canonical spins 0, 1 and 2, 3, i.e. on
+// (v'_u + v'_d) / sqrt(2) and (v'_u - v'_d) / sqrt(2); the two factors
+// 1 / sqrt(2) of the rotations in and out combine to one 1 / 2.
 template <int P>
 __device__ __forceinline__ void clover_mul(const char *parity_base, int vh, int cb,
                                            Cx<typename Prec<P>::real> (&v)[12]) {
     using R = typename Prec<P>::real;
+    Cx<R> w[12];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        w[k] = {v[k].re + v[6 + k].re, v[k].im + v[6 + k].im};
+        w[6 + k] = {v[k].re - v[6 + k].re, v[k].im - v[6 + k].im};
+    }
+    Cx<R> o[2][6];
 #pragma unroll
     for (int chi = 0; chi < 2; ++chi) {
         R m[kCloverReals];
         CloverIO<P>::load(parity_base + chi * clover_block_bytes(P, vh), vh, cb, m);
-        Cx<R> o[6];
-        herm6_mul(m, v + 6 * chi, o);
+        herm6_mul(m, w + 6 * chi, o[chi]);
+    }
+    const R h = R(0.5);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) v[6 * chi + i] = o[i];
+    for (int k = 0; k < 6; ++k) {
+        v[k] = {h * (o[0][k].re + o[1][k].re), h * (o[0][k].im + o[1][k].im)};
+        v[6 + k] = {h * (o[0][k].re - o[1][k].re), h * (o[0][k].im - o[1][k].im)};
     }
 }
 

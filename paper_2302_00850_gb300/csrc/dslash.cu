@@ -192,6 +192,16 @@ cudaError_t launch_dslash(int prec, int recon, DslashArgs &A, int nparity, bool 
         }
     }
     if (g_tune_only) return cudaSuccess;
+    // COLA_DSLASH_NR=n forces n right-hand sides per thread where the kernel
+    // supports it (tests of the multi-right-hand-side kernel)
+    static const int env_nr = [] {
+        const char *e = getenv("COLA_DSLASH_NR");
+        return e ? atoi(e) : 0;
+    }();
+    if (env_nr > 0 && mrhs_supported(prec, env_nr) && staged_depth(prec) == 0 && A.nrhs > 1) {
+        A.rhs_per_thread = env_nr;
+        if (A.rhs_per_block * env_nr > A.nrhs) A.rhs_per_block = 1;
+    }
     if (prec != COLA_F64 && staged_depth(prec) > 0 && block_x * A.rhs_per_block != kStagedThreads) {
         // the staged kernel's shared-memory layout is built for kStagedThreads threads
         A.rhs_per_block = std::min(A.rhs_per_block, 4);

@@ -19,7 +19,12 @@
 // with s = +1 for H and s = -1 for H^dag (projectors swapped).  Each
 // projector has rank two, so the SU(3) multiply acts on a two-spinor and
 // the other two spin rows are rebuilt from it (spin projection and
-// reconstruction, gamma matrices in the DeGrand-Rossi basis).
+// reconstruction).  Packed spinors are in the rotated spin basis of the
+// packing (psi' = S psi, S = (gamma_t + gamma5) / sqrt(2)), where
+// gamma_x, gamma_y, gamma_z are minus their DeGrand-Rossi forms and
+// gamma_t = diag(1, 1, -1, -1): a time hop's projector 1 +- gamma_t is twice
+// the projection on spins 0, 1 or on spins 2, 3, with nothing to add and
+// half the rows to accumulate.
 #pragma once
 
 #include <type_traits>
@@ -44,9 +49,10 @@ __device__ __forceinline__ Cx<R> add_s(Cx<R> a, Cx<R> b) {
     else return {a.re - b.re, a.im - b.im};
 }
 
-// Two-spinor h = rows 0, 1 of (1 + S gamma_mu) psi.
+// Two-spinor h = rows 0, 1 of (1 + S gamma_mu) psi, gamma_mu in the
+// DeGrand-Rossi (canonical) basis.
 template <int MU, int S, typename R>
-__device__ __forceinline__ void project(const Cx<R> (&psi)[12], Cx<R> (&h)[2][3]) {
+__device__ __forceinline__ void project_chiral(const Cx<R> (&psi)[12], Cx<R> (&h)[2][3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const Cx<R> p0 = psi[a], p1 = psi[3 + a], p2 = psi[6 + a], p3 = psi[9 + a];
@@ -66,16 +72,35 @@ __device__ __forceinline__ void project(const Cx<R> (&psi)[12], Cx<R> (&h)[2][3]
     }
 }
 
+// Two-spinor h of (1 + S gamma_mu) psi in the packed basis: for the space
+// directions the canonical projection with -S; for time the spins the
+// projector keeps (0, 1 for S = +1, 2, 3 for S = -1), the factor 2 being
+// applied at accumulation.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Cx<R> (&psi)[12], Cx<R> (&h)[2][3]) {
+    if constexpr (MU < 3) {
+        project_chiral<MU, -S>(psi, h);
+    } else {
+        constexpr int off = S > 0 ? 0 : 6;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            h[0][a] = psi[off + a];
+            h[1][a] = psi[off + 3 + a];
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ Cx<R> times_i(Cx<R> a, int s) {  // s*i*a
     return s > 0 ? Cx<R>{-a.im, a.re} : Cx<R>{a.im, -a.re};
 }
 
-// acc += sc * (full spinor rebuilt from w = U h); rows 2, 3 follow from rows 0, 1.
-// sc carries the neighbour's FP16 site scale and a real boundary phase, so
-// both cost nothing beyond the fused multiply-adds of the accumulation.
+// acc += sc * (full spinor rebuilt from w = U h); rows 2, 3 follow from rows 0, 1
+// (canonical basis).  sc carries the neighbour's FP16 site scale and a real
+// boundary phase, so both cost nothing beyond the fused multiply-adds of
+// the accumulation.
 template <int MU, int S, typename R>
-__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3], R sc) {
+__device__ __forceinline__ void accumulate_chiral(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3], R sc) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         acc[a].re = fma(sc, w[0][a].re, acc[a].re);
@@ -103,6 +128,25 @@ __device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2]
             acc[9 + a].re = fma(S * sc, w[1][a].re, acc[9 + a].re);
             acc[9 + a].im = fma(S * sc, w[1][a].im, acc[9 + a].im);
         }
+    }
+}
+
+// The same in the packed basis: for time, 2 sc w goes to the two spins the
+// projector keeps and nothing to the others.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&w)[2][3], R sc) {
+    if constexpr (MU < 3) {
+        accumulate_chiral<MU, -S>(acc, w, sc);
+    } else {
+        constexpr int off = S > 0 ? 0 : 6;
+        const R s2 = R(2) * sc;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc[off + 3 * k + a].re = fma(s2, w[k][a].re, acc[off + 3 * k + a].re);
+                acc[off + 3 * k + a].im = fma(s2, w[k][a].im, acc[off + 3 * k + a].im);
+            }
     }
 }
 
@@ -163,7 +207,8 @@ __device__ __forceinline__ void accumulate01(Cx<R> (&acc)[12], const Cx<R> (&c)[
     }
 }
 
-// Rows 2 and 3 of the reconstruction of d with projector sign S, times sc.
+// Rows 2 and 3 of the reconstruction of d with projector sign S, times sc
+// (canonical basis; the space directions of the packed basis use -S).
 template <int MU, int S, typename R>
 __device__ __forceinline__ void accumulate23(Cx<R> (&acc)[12], const Cx<R> (&d)[2][3], R sc) {
 #pragma unroll
@@ -308,7 +353,8 @@ __device__ __forceinline__ void hop_pair_apply(const Geom &g, const Cx<typename 
     constexpr int SB = -SF;
     Cx<R> wf[2][3];
     su3_mul(uf, hf, wf);
-    if (P != COLA_F16 && !edge_f && !edge_b) {
+    // time hops each fill half the rows, so the pairing below only pays for space
+    if (MU < 3 && P != COLA_F16 && !edge_f && !edge_b) {
         Cx<R> cs[2][3];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -323,7 +369,7 @@ __device__ __forceinline__ void hop_pair_apply(const Geom &g, const Cx<typename 
                 wf[k][a].im = fma(R(2), wf[k][a].im, -cs[k][a].im);
             }
         accumulate01(acc, cs, bs);
-        accumulate23<MU, SF>(acc, wf, bs);
+        accumulate23<MU, -SF>(acc, wf, bs);  // packed basis: gamma_mu' = -gamma_mu for space
     } else {
         R sf = scf * bs, sb = scb * bs;
         if (edge_f) boundary_phase(g, MU, false, wf, sf);
@@ -465,11 +511,21 @@ __device__ __forceinline__ Cx<float> h2cx(uint32_t w) {
     return {f.x, f.y};
 }
 
-// Two-spinor h = rows 0, 1 of (1 + S gamma_mu) psi from a stored FP16 spinor
-// (unscaled; the site scale is applied with the hop's scale).  The same
-// combinations as project<MU, S>.
-template <int MU, int S>
+// Two-spinor h of (1 + S gamma_mu) psi from a stored FP16 spinor in the
+// packed basis (unscaled; the site scale is applied with the hop's scale).
+// The same combinations as project<MU, S>.
+template <int MU, int SP>
 __device__ __forceinline__ void project_h16(const uint32_t (&p)[12], Cx<float> (&h)[2][3]) {
+    if constexpr (MU == 3) {  // packed basis: the kept spins, converted
+        constexpr int off = SP > 0 ? 0 : 6;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            h[0][a] = h2cx(p[off + a]);
+            h[1][a] = h2cx(p[off + 3 + a]);
+        }
+        return;
+    }
+    constexpr int S = -SP;  // packed basis: gamma_mu' = -gamma_mu for space
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if constexpr (MU == 0) {

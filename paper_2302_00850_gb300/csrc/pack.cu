@@ -5,9 +5,27 @@
 // parity, one array per storage group over the Vh = V/2 sites of that parity
 // (checkerboard index cb = i / 2), so that a warp reading one group for 32
 // consecutive sites issues one coalesced transaction.
+//
+// Packed spinors hold psi' = S psi, S = (gamma_t + gamma5) / sqrt(2), a
+// unitary and Hermitian spin rotation (S S = 1): with u = spins 0, 1 and
+// d = spins 2, 3 of the canonical chiral basis, u' = (u + d) / sqrt(2) and
+// d' = (u - d) / sqrt(2).  In that basis gamma_t is diag(1, 1, -1, -1), so
+// the time hops of the hopping term project by selecting two spins, and
+// gamma_x, gamma_y, gamma_z are minus their canonical forms.
 #include "cola_impl.h"
 
 namespace cola {
+
+// s <- S s on one site (canonical <-> packed spin basis; S is its own inverse)
+__device__ __forceinline__ void spin_rotate(Cx<double> (&s)[12]) {
+    constexpr double r = 0.70710678118654752440;  // 1 / sqrt(2)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const Cx<double> u = s[k], d = s[6 + k];
+        s[k] = {(u.re + d.re) * r, (u.im + d.im) * r};
+        s[6 + k] = {(u.re - d.re) * r, (u.im - d.im) * r};
+    }
+}
 
 __device__ __forceinline__ void site_parity_cb(const Geom &g, int i, int &par, int &cb) {
     int x = i % g.L[0];
@@ -30,12 +48,13 @@ __global__ void pack_spinor_kernel(const Geom g, void *packed, const double2 *ca
     site_parity_cb(g, i, par, cb);
     if (!((pmask >> par) & 1)) return;
     const double2 *src = canon + ((size_t)rhs * g.V + i) * 12;
+    Cx<double> sd[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) sd[c] = {src[c].x, src[c].y};
+    spin_rotate(sd);
     Cx<R> s[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-        double2 v = src[c];
-        s[c] = {(R)v.x, (R)v.y};
-    }
+    for (int c = 0; c < 12; ++c) s[c] = {(R)sd[c].re, (R)sd[c].im};
     const size_t pbytes = spinor_parity_bytes(P, g.Vh);
     char *dst = static_cast<char *>(packed) + (size_t)rhs * 2 * pbytes + par * pbytes;
     SpinorIO<P>::store(dst, g.Vh, cb, s);
@@ -57,9 +76,13 @@ __global__ void unpack_spinor_kernel(const Geom g, double2 *canon, const void *p
     const char *src = static_cast<const char *>(packed) + (size_t)rhs * 2 * pbytes + par * pbytes;
     Cx<R> s[12];
     SpinorIO<P>::load(src, g.Vh, cb, s);
+    Cx<double> sd[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) sd[c] = {(double)s[c].re, (double)s[c].im};
+    spin_rotate(sd);
     double2 *dst = canon + ((size_t)rhs * g.V + i) * 12;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)s[c].re, (double)s[c].im);
+    for (int c = 0; c < 12; ++c) dst[c] = make_double2(sd[c].re, sd[c].im);
 }
 
 template <int P, int RECON>
