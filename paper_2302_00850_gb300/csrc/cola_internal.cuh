@@ -158,6 +158,14 @@ __device__ __forceinline__ void cmac(Cx<R> &acc, Cx<R> a, Cx<R> b) {
     acc.im = fma(a.re, b.im, acc.im);
     acc.im = fma(a.im, b.re, acc.im);
 }
+// acc -= a * b
+template <typename R>
+__device__ __forceinline__ void cmsub(Cx<R> &acc, Cx<R> a, Cx<R> b) {
+    acc.re = fma(-a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(-a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
 // acc += conj(a) * b
 template <typename R>
 __device__ __forceinline__ void cmac_conj(Cx<R> &acc, Cx<R> a, Cx<R> b) {
@@ -194,15 +202,17 @@ __host__ __device__ constexpr size_t spinor_parity_bytes(int prec, int vh) {
 }
 
 // Number of storage groups of one link (3x3 or its first two rows).
-__host__ __device__ constexpr int link_groups(int prec, int recon) {
-    return prec == COLA_F64 ? (recon == 12 ? 6 : 9) : (recon == 12 ? 3 : 5);
-}
-__host__ __device__ constexpr size_t link_group_bytes(int prec) {
-    return prec == COLA_F64 ? 16 : prec == COLA_F32 ? 16 : 8;
+// FP16 links: 16-byte groups of four complexes, then one 8-byte group.
+__host__ __device__ constexpr int link16_groups_f16(int recon) { return recon == 12 ? 1 : 2; }
+// Bytes per site of one direction of the packed links (the layout is below).
+__host__ __device__ constexpr size_t link_site_bytes(int prec, int recon) {
+    return prec == COLA_F64 ? (recon == 12 ? 6 : 9) * 16
+         : prec == COLA_F32 ? (recon == 12 ? 3 : 5) * 16
+                            : link16_groups_f16(recon) * 16 + 8;
 }
 // Bytes of one direction of one parity of the packed links.
 __host__ __device__ constexpr size_t link_dir_bytes(int prec, int recon, int vh) {
-    return (size_t)link_groups(prec, recon) * link_group_bytes(prec) * vh;
+    return link_site_bytes(prec, recon) * vh;
 }
 
 // --------------------------------------------------------- spinor access --
@@ -318,25 +328,32 @@ struct SpinorIO<COLA_F16> {
 };
 
 // ----------------------------------------------------------- link access --
-// One direction of one parity of the packed links: link_groups() arrays over
-// Vh sites.  F64 groups are one complex (double2); F32 groups two complexes
-// (float4); F16 groups two complexes (4 halves, 8 bytes).  Entries are
-// row-major u00 u01 u02 u10 ...; with recon 18 the last group of F32/F16 is
-// half padding.
+// One direction of one parity of the packed links: arrays of groups over Vh
+// sites.  F64 groups are one complex (double2); F32 groups two complexes
+// (float4).  F16 groups are four complexes (16 bytes: 8 halves), then one
+// group of the last two complexes (8 bytes), so that a link is two 16-byte
+// and 8-byte loads (recon 12: 16 + 8 bytes; recon 18: 16 + 16 + 8).
+// Entries are row-major u00 u01 u02 u10 ...; with recon 18 the last group of
+// F32/F16 is half padding.
 template <int P, int RECON>
 struct LinkIO;
 
 template <typename R>
 __device__ __forceinline__ void reconstruct_row2(Cx<R> (&u)[9]) {
-    // row2 = conj(row0 x row1), exact for SU(3)
-    Cx<R> a = cmul(u[1], u[5]), b = cmul(u[2], u[4]);
-    u[6] = {a.re - b.re, -(a.im - b.im)};
-    a = cmul(u[2], u[3]);
-    b = cmul(u[0], u[5]);
-    u[7] = {a.re - b.re, -(a.im - b.im)};
-    a = cmul(u[0], u[4]);
-    b = cmul(u[1], u[3]);
-    u[8] = {a.re - b.re, -(a.im - b.im)};
+    // row2 = conj(row0 x row1), exact for SU(3).  Each component is one
+    // multiply-add chain: t = a b, then t -= c d continuing it (8 operations
+    // instead of two products and a subtraction).
+    Cx<R> t = cmul(u[1], u[5]);
+    cmsub(t, u[2], u[4]);
+    Cx<R> r6 = {t.re, -t.im};
+    t = cmul(u[2], u[3]);
+    cmsub(t, u[0], u[5]);
+    Cx<R> r7 = {t.re, -t.im};
+    t = cmul(u[0], u[4]);
+    cmsub(t, u[1], u[3]);
+    u[6] = r6;
+    u[7] = r7;
+    u[8] = {t.re, -t.im};
 }
 
 template <int RECON>
@@ -381,14 +398,25 @@ struct LinkIO<COLA_F32, RECON> {
 template <int RECON>
 struct LinkIO<COLA_F16, RECON> {
     __device__ static __forceinline__ void load(const void *dir_base, int vh, int cb, Cx<float> (&u)[9]) {
-        const uint2 *p = reinterpret_cast<const uint2 *>(dir_base);
-        constexpr int n = RECON == 12 ? 3 : 5;
+        constexpr int n16 = link16_groups_f16(RECON);
+        const uint4 *p = reinterpret_cast<const uint4 *>(dir_base);
+        uint32_t w[4 * n16 + 2];
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
-            uint2 v = __ldg(p + (size_t)k * vh + cb);
-            float2 a = h2f(v.x), b = h2f(v.y);
-            if (2 * k < 9) u[2 * k] = {a.x, a.y};
-            if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
+        for (int k = 0; k < n16; ++k) {
+            const uint4 v = __ldg(p + (size_t)k * vh + cb);
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        }
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p + (size_t)n16 * vh) + cb);
+        w[4 * n16] = v.x;
+        w[4 * n16 + 1] = v.y;
+        constexpr int ncplx = RECON == 12 ? 6 : 9;
+#pragma unroll
+        for (int k = 0; k < ncplx; ++k) {
+            const float2 a = h2f(w[k]);
+            u[k] = {a.x, a.y};
         }
         if constexpr (RECON == 12) reconstruct_row2(u);
     }

@@ -397,6 +397,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// The same without allocating in L1 (.cg), for the neighbour spinors: L2
+// serves their reuse, and the copies ran faster at 32^3x64 than through L1
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -412,14 +418,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Raw bytes of one hop: spinor chunks of 16 B (+ one 4-byte FP16 scale) and
-// link chunks of 16 B (FP32) or 8 B (FP16).
+// link chunks of 16 B (FP32: two complexes each; FP16: four) plus, for
+// FP16, one 8-byte chunk of the last two complexes.
 template <int P, int RECON>
 struct HopLayout {
     static constexpr int spin16 = P == COLA_F32 ? 6 : 3;
     static constexpr int scale4 = P == COLA_F16 ? 1 : 0;
-    static constexpr int link_chunks = RECON == 12 ? 3 : 5;
-    static constexpr int link_bytes = P == COLA_F32 ? 16 : 8;
-    static constexpr int bytes = spin16 * 16 + scale4 * 4 + link_chunks * link_bytes;
+    static constexpr int link16 = P == COLA_F32 ? (RECON == 12 ? 3 : 5) : link16_groups_f16(RECON);
+    static constexpr int link8 = P == COLA_F16 ? 1 : 0;
+    static constexpr int bytes = spin16 * 16 + scale4 * 4 + link16 * 16 + link8 * 8;
 };
 
 // The staged kernel always runs kStagedThreads threads per block (sites x
@@ -436,8 +443,11 @@ struct Stage {
     __device__ float *scale(int tid) const {
         return reinterpret_cast<float *>(base + L::spin16 * 16 * T) + tid;
     }
-    __device__ char *link(int k, int tid) const {
-        return base + (L::spin16 * 16 + L::scale4 * 4) * T + (k * T + tid) * L::link_bytes;
+    __device__ uint4 *link16(int k, int tid) const {
+        return reinterpret_cast<uint4 *>(base + (L::spin16 * 16 + L::scale4 * 4) * T) + k * T + tid;
+    }
+    __device__ uint2 *link8(int tid) const {
+        return reinterpret_cast<uint2 *>(base + (L::spin16 * 16 + L::scale4 * 4 + L::link16 * 16) * T) + tid;
     }
 };
 
@@ -457,16 +467,13 @@ __device__ __forceinline__ void stage_issue(const DslashLat &A, const Coord &c, 
     const Geom &g = A.g;
     const int nb = nbr_cb<MU, DIR>(g, c, cb);
 #pragma unroll
-    for (int k = 0; k < L::spin16; ++k) cp_async16(st.spin(k, tid), in + ((size_t)k * g.Vh + nb) * 16);
+    for (int k = 0; k < L::spin16; ++k) cp_async16_cg(st.spin(k, tid), in + ((size_t)k * g.Vh + nb) * 16);
     if constexpr (L::scale4) cp_async4(st.scale(tid), in + (size_t)L::spin16 * 16 * g.Vh + (size_t)nb * 4);
     const char *lb = (DIR > 0 ? links_out : links_in) + MU * A.link_dir_stride;
     const int lcb = DIR > 0 ? cb : nb;
 #pragma unroll
-    for (int k = 0; k < L::link_chunks; ++k) {
-        const char *src = lb + ((size_t)k * g.Vh + lcb) * L::link_bytes;
-        if constexpr (L::link_bytes == 16) cp_async16(st.link(k, tid), src);
-        else cp_async8(st.link(k, tid), src);
-    }
+    for (int k = 0; k < L::link16; ++k) cp_async16(st.link16(k, tid), lb + ((size_t)k * g.Vh + lcb) * 16);
+    if constexpr (L::link8) cp_async8(st.link8(tid), lb + (size_t)L::link16 * 16 * g.Vh + (size_t)lcb * 8);
 }
 
 // FP16 spin projection straight from storage.  PTX for sm_100 and later
@@ -549,10 +556,10 @@ __device__ __forceinline__ void project_h16(const uint32_t (&p)[12], Cx<float> (
 template <int P, int RECON>
 struct HopRaw {
     using L = HopLayout<P, RECON>;
-    using LinkWord = typename std::conditional<L::link_bytes == 16, uint4, uint2>::type;
     uint4 spin[L::spin16];
     float scale;
-    LinkWord link[L::link_chunks];
+    uint4 link16[L::link16];
+    uint2 link8;
 };
 
 template <int P, int RECON>
@@ -563,7 +570,8 @@ __device__ __forceinline__ HopRaw<P, RECON> stage_load_raw(const Stage<P, RECON>
     for (int k = 0; k < H::L::spin16; ++k) r.spin[k] = *st.spin(k, tid);
     r.scale = H::L::scale4 ? *st.scale(tid) : 1.0f;
 #pragma unroll
-    for (int k = 0; k < H::L::link_chunks; ++k) r.link[k] = *reinterpret_cast<const typename H::LinkWord *>(st.link(k, tid));
+    for (int k = 0; k < H::L::link16; ++k) r.link16[k] = *st.link16(k, tid);
+    r.link8 = H::L::link8 ? *st.link8(tid) : make_uint2(0u, 0u);
     return r;
 }
 
@@ -601,17 +609,22 @@ __device__ __forceinline__ void hop_compute(const Geom &g, const Coord &c, const
     }
     Cx<float> u[9];
     if constexpr (P == COLA_F16) {
+        uint32_t w[4 * L::link16 + 2];
 #pragma unroll
-        for (int k = 0; k < L::link_chunks; ++k) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(&r.link[k]);
-            float2 a = h2f(v.x), b = h2f(v.y);
-            if (2 * k < 9) u[2 * k] = {a.x, a.y};
-            if (2 * k + 1 < 9) u[2 * k + 1] = {b.x, b.y};
+        for (int k = 0; k < L::link16; ++k) {
+            w[4 * k] = r.link16[k].x;
+            w[4 * k + 1] = r.link16[k].y;
+            w[4 * k + 2] = r.link16[k].z;
+            w[4 * k + 3] = r.link16[k].w;
         }
+        w[4 * L::link16] = r.link8.x;
+        w[4 * L::link16 + 1] = r.link8.y;
+#pragma unroll
+        for (int k = 0; k < (RECON == 12 ? 6 : 9); ++k) u[k] = h2cx(w[k]);
     } else {
 #pragma unroll
-        for (int k = 0; k < L::link_chunks; ++k) {
-            const float4 v = *reinterpret_cast<const float4 *>(&r.link[k]);
+        for (int k = 0; k < L::link16; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(&r.link16[k]);
             if (2 * k < 9) u[2 * k] = {v.x, v.y};
             if (2 * k + 1 < 9) u[2 * k + 1] = {v.z, v.w};
         }

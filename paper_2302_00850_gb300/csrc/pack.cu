@@ -107,17 +107,16 @@ __global__ void pack_gauge_kernel(const Geom g, void *packed, const double2 *can
             double2 b = (2 * k + 1 < ncplx) ? u[2 * k + 1] : make_double2(0.0, 0.0);
             d[(size_t)k * g.Vh + cb] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
         }
-    } else {
-        uint2 *d = reinterpret_cast<uint2 *>(base);
-        constexpr int ng = RECON == 12 ? 3 : 5;
-        for (int k = 0; k < ng; ++k) {
-            double2 a = u[2 * k];
-            double2 b = (2 * k + 1 < ncplx) ? u[2 * k + 1] : make_double2(0.0, 0.0);
-            uint2 w;
-            w.x = f2h((float)a.x, (float)a.y);
-            w.y = f2h((float)b.x, (float)b.y);
-            d[(size_t)k * g.Vh + cb] = w;
+    } else {  // 16-byte groups of four complexes, then the last two complexes (8 bytes)
+        constexpr int n16 = link16_groups_f16(RECON);
+        uint32_t w[4 * n16 + 2];
+        for (int k = 0; k < 4 * n16 + 2; ++k) {
+            const double2 a = k < ncplx ? u[k] : make_double2(0.0, 0.0);
+            w[k] = f2h((float)a.x, (float)a.y);
         }
+        uint4 *d = reinterpret_cast<uint4 *>(base);
+        for (int k = 0; k < n16; ++k) d[(size_t)k * g.Vh + cb] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        reinterpret_cast<uint2 *>(d + (size_t)n16 * g.Vh)[cb] = make_uint2(w[4 * n16], w[4 * n16 + 1]);
     }
 }
 
