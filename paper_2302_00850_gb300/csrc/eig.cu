@@ -27,10 +27,13 @@
 // fixed order (block partials, one finishing block per result).  The
 // minimisation of each vector runs on the device: its scalars (the rotation
 // of the line search, beta, the projection coefficients, the stopping test)
-// are computed by one-thread control kernels into device memory, the linear
-// combinations read their coefficients from there, and the CG loop is a
-// while node of a CUDA graph (one graph per vector index, built on first use
-// in a call).  The host launches the graphs of a sweep back to back, runs the
+// are computed into device memory by one thread after the dot products they
+// need are finished, the linear combinations read their coefficients from
+// there, and the CG loop is a while node of a CUDA graph (one graph per
+// vector index, built on first use in a call).  A CG step is 7 launches
+// besides the operator: the rotation, the gradient and its dot products
+// share one pass over the sites, as do the projection, the new direction and
+// the dot products the next step starts from.  The host launches the graphs of a sweep back to back, runs the
 // Rayleigh-Ritz step, and reads the residuals once per sweep.
 #include <algorithm>
 #include <chrono>
@@ -78,6 +81,7 @@ struct DotArgs {
     const char *b[kMaxTerms];
     double *partials;  // [n][nb][2]
     int nb;
+    unsigned re_only;  // bit k: pair k needs the real part only (its imaginary partial is 0)
 };
 
 // Pairs are taken four at a time with one block reduction per group, and a
@@ -86,11 +90,76 @@ struct DotArgs {
 // block_sum: warp butterflies, then the warps in order.
 constexpr int kDotGroup = 4;
 
+// Block partials of one group of kDotGroup dots (re, im in v): warp
+// butterflies, then the warps in order; results k0 .. min(k0 + kDotGroup, n)
+// go to partials[k][blockIdx.x].  Every thread of the block calls it.
+__device__ __forceinline__ void group_partials(double (&v)[2 * kDotGroup], int k0, int n, double *partials, int nb,
+                                               double (*sh)[2 * kDotGroup]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 2 * kDotGroup; ++q) v[q] = warp_allsum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 2 * kDotGroup; ++q) sh[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 2 * kDotGroup) {
+        const int k = k0 + (int)threadIdx.x / 2;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[w][threadIdx.x];
+        if (k < n) partials[((size_t)k * nb + blockIdx.x) * 2 + (threadIdx.x & 1)] = t;
+    }
+    __syncthreads();
+}
+
+// conj(a) b accumulated over the 12 components of one site, in the order
+// every dot product of the eigensolver uses
+__device__ __forceinline__ void site_dot(const Cx<double> (&a)[12], const Cx<double> (&b)[12], double &re,
+                                         double &im) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        re = fma(a[c].re, b[c].re, fma(a[c].im, b[c].im, re));
+        im = fma(a[c].re, b[c].im, fma(-a[c].im, b[c].re, im));
+    }
+}
+
+// The real part alone (for |a|^2, and for dots whose imaginary part no
+// step uses): the same multiply-adds as site_dot's real part.
+__device__ __forceinline__ void site_dot_re(const Cx<double> (&a)[12], const Cx<double> (&b)[12], double &re) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) re = fma(a[c].re, b[c].re, fma(a[c].im, b[c].im, re));
+}
+
+// acc += w x over a site.  The vector work of the eigensolver runs on the
+// FP64 pipe (one complex multiply-add is 4 FP64 operations per component, at
+// 1/64 of the FP32 rate), so a real w takes the 2 multiply-adds that its
+// non-zero part needs (the zero imaginary part only adds exact zeros), and
+// w = 1 into an empty accumulator is a copy.
+__device__ __forceinline__ void site_mac(Cx<double> (&acc)[12], double2 w, const Cx<double> (&x)[12], bool first) {
+    if (w.y == 0.0) {
+        if (first && w.x == 1.0) {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = x[c];
+            return;
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            acc[c].re = fma(w.x, x[c].re, first ? 0.0 : acc[c].re);
+            acc[c].im = fma(w.x, x[c].im, first ? 0.0 : acc[c].im);
+        }
+        return;
+    }
+    const Cx<double> cw = {w.x, w.y};
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        if (first) acc[c] = {0.0, 0.0};
+        cmac(acc[c], cw, x[c]);
+    }
+}
+
 __global__ void __launch_bounds__(kBlk, 2) dots_kernel(const __grid_constant__ DotArgs A) {
     __shared__ double sh[kBlk / 32][2 * kDotGroup];
     int par, cb;
     const bool ok = site(A.F, par, cb);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const char *pa = nullptr, *pb = nullptr;
     Cx<double> x[12], y[12];
     for (int k0 = 0; k0 < A.n; k0 += kDotGroup) {
@@ -108,28 +177,13 @@ __global__ void __launch_bounds__(kBlk, 2) dots_kernel(const __grid_constant__ D
                     pb = A.b[k];
                     SpinorIO<COLA_F64>::load(at(pb, A.F.vh, par), A.F.vh, cb, y);
                 }
-#pragma unroll
-                for (int c = 0; c < 12; ++c) {
-                    re = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, re));
-                    im = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, im));
-                }
+                if (k < 32 && ((A.re_only >> k) & 1u)) site_dot_re(x, y, re);
+                else site_dot(x, y, re, im);
             }
             v[2 * q] = re;
             v[2 * q + 1] = im;
         }
-#pragma unroll
-        for (int q = 0; q < 2 * kDotGroup; ++q) v[q] = warp_allsum(v[q]);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 2 * kDotGroup; ++q) sh[warp][q] = v[q];
-        __syncthreads();
-        if (threadIdx.x < 2 * kDotGroup) {
-            const int k = k0 + (int)threadIdx.x / 2;
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += sh[w][threadIdx.x];
-            if (k < A.n) A.partials[((size_t)k * A.nb + blockIdx.x) * 2 + (threadIdx.x & 1)] = t;
-        }
-        __syncthreads();
+        group_partials(v, k0, A.n, A.partials, A.nb, sh);
     }
 }
 
@@ -166,9 +220,7 @@ __global__ void __launch_bounds__(kBlk) lincomb_kernel(const __grid_constant__ C
     for (int k = 0; k < A.n; ++k) {
         Cx<double> x[12];
         SpinorIO<COLA_F64>::load(at(A.in[k], A.F.vh, par), A.F.vh, cb, x);
-        const Cx<double> w = {A.c[k].x, A.c[k].y};
-#pragma unroll
-        for (int c = 0; c < 12; ++c) cmac(acc[c], w, x[c]);
+        site_mac(acc, A.c[k], x, k == 0);
     }
     SpinorIO<COLA_F64>::store(const_cast<char *>(at(A.out, A.F.vh, par)), A.F.vh, cb, acc);
 }
@@ -208,10 +260,7 @@ __global__ void __launch_bounds__(kBlk) lincomb_dev_kernel(const __grid_constant
     for (int k = 0; k < A.n; ++k) {
         Cx<double> x[12];
         SpinorIO<COLA_F64>::load(at(A.in[k], A.F.vh, par), A.F.vh, cb, x);
-        const double2 cw = A.e->coef[A.set][k];
-        const Cx<double> w = {cw.x, cw.y};
-#pragma unroll
-        for (int c = 0; c < 12; ++c) cmac(acc[c], w, x[c]);
+        site_mac(acc, A.e->coef[A.set][k], x, k == 0);
     }
     SpinorIO<COLA_F64>::store(const_cast<char *>(at(A.out, A.F.vh, par)), A.F.vh, cb, acc);
 }
@@ -241,10 +290,10 @@ __device__ __forceinline__ void gradient_norm(EigDev &e, const double2 *d, int j
     e.gg_new = fmax(n2, 0.0);
 }
 
-// One-thread control steps; d holds the latest finished dot products.
+// The control steps (one thread); d holds the latest finished dot products.
 template <int STEP>
-__global__ void eig_ctl_kernel(EigDev *ep, const double2 *d, const CtlParams p, cudaGraphConditionalHandle h) {
-    EigDev &e = *ep;
+__device__ __forceinline__ void ctl_step(EigDev &e, const double2 *d, const CtlParams &p,
+                                         cudaGraphConditionalHandle h) {
     if constexpr (STEP == CTL_PROJ) {  // x -= sum_i <v_i, x> v_i
         e.coef[C_PROJ][0] = make_double2(1.0, 0.0);
         for (int i = 0; i < p.j; ++i) e.coef[C_PROJ][1 + i] = make_double2(-d[i].x, -d[i].y);
@@ -310,6 +359,163 @@ __global__ void eig_ctl_kernel(EigDev *ep, const double2 *d, const CtlParams p, 
         e.cont = !e.stop && !e.halt && keep_going(e, p);
         cudaGraphSetConditional(h, e.cont ? 1u : 0u);
     }
+}
+
+template <int STEP>
+__global__ void eig_ctl_kernel(EigDev *ep, const double2 *d, const CtlParams p, cudaGraphConditionalHandle h) {
+    ctl_step<STEP>(*ep, d, p, h);
+}
+
+// The CG loop's fused steps.  fin_ctl: one block sums the partials of n dot
+// products in block order (as dots_finish_kernel does) and thread 0 runs a
+// control step on them (CTL_GRAD is followed by CTL_END, which depends only
+// on it).  rot_grad_dots: the rotation of the line search and the new
+// gradient, x' = r0 x + r1 p^, y' = r0 y + r1 z, g = y' - mu x', with the
+// partials of <v_i, g> (i < j), |g|^2 and <x', p^> in the same pass over the
+// sites.  proj_dir_dots: the projection of g on the complement of
+// v_0 .. v_{j-1} and the new direction p = g' + beta (p - <x', p> x'), with the
+// partials of <x, p> and |p|^2 that the next step starts from.  Their linear
+// combinations and dot products are those of lincomb_dev_kernel and
+// dots_kernel in the same order (real coefficients and real dots skip only
+// exact zeros), so the results are unchanged; the step runs 7 small
+// launches instead of 16.
+template <int STEP>
+__global__ void __launch_bounds__(kBlk) fin_ctl_kernel(EigDev *ep, const double *partials, int nb, int n, double2 *d,
+                                                       const CtlParams p, cudaGraphConditionalHandle h) {
+    // warp w of block_sum holds threads 32 w + lane: one warp per result
+    // replays them in turn, so each sum has block_sum's order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < n; k += nw) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            double re = 0.0, im = 0.0;
+            for (int b = 32 * w + lane; b < nb; b += blockDim.x) {
+                re += partials[((size_t)k * nb + b) * 2];
+                im += partials[((size_t)k * nb + b) * 2 + 1];
+            }
+            tr += warp_allsum(re);
+            ti += warp_allsum(im);
+        }
+        if (lane == 0) d[k] = make_double2(tr, ti);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl_step<STEP>(*ep, d, p, h);
+        if constexpr (STEP == CTL_GRAD) ctl_step<CTL_END>(*ep, d, p, h);
+    }
+}
+
+struct StepArgs {
+    Fields F;
+    int j;
+    char *x, *y, *g, *p;
+    const char *z;
+    const char *v[kMaxTerms];
+    const EigDev *e;
+    double *partials;
+    int nb;
+};
+
+__device__ __forceinline__ void load_site(const char *f, const Fields &F, int par, int cb, Cx<double> (&s)[12]) {
+    SpinorIO<COLA_F64>::load(at(f, F.vh, par), F.vh, cb, s);
+}
+__device__ __forceinline__ void store_site(char *f, const Fields &F, int par, int cb, const Cx<double> (&s)[12]) {
+    SpinorIO<COLA_F64>::store(const_cast<char *>(at(f, F.vh, par)), F.vh, cb, s);
+}
+// The basis dots <v_i, f> (i < j) of a register spinor f, then the two extra
+// results (re, im pairs in extra), as partials j, j + 1.
+__device__ __forceinline__ void basis_partials(const StepArgs &A, bool ok, int par, int cb, const Cx<double> (&f)[12],
+                                               const double (&extra)[4], double (*sh)[2 * kDotGroup]) {
+    const int n = A.j + 2;
+    for (int k0 = 0; k0 < n; k0 += kDotGroup) {
+        double v[2 * kDotGroup];
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) {
+            const int k = k0 + q;
+            double re = 0.0, im = 0.0;
+            if (k < A.j) {
+                if (ok) {
+                    Cx<double> a[12];
+                    load_site(A.v[k], A.F, par, cb, a);
+                    site_dot(a, f, re, im);
+                }
+            } else if (k < n) {
+                re = extra[2 * (k - A.j)];
+                im = extra[2 * (k - A.j) + 1];
+            }
+            v[2 * q] = re;
+            v[2 * q + 1] = im;
+        }
+        group_partials(v, k0, n, A.partials, A.nb, sh);
+    }
+}
+
+// Four spinors and the new gradient are live at once: one block per SM keeps
+// them in registers.
+__global__ void __launch_bounds__(kBlk, 1) rot_grad_dots_kernel(const __grid_constant__ StepArgs A) {
+    __shared__ double sh[kBlk / 32][2 * kDotGroup];
+    if (A.e->halt || A.e->stop) return;  // the same for every block
+    int par, cb;
+    const bool ok = site(A.F, par, cb);
+    Cx<double> g[12];
+    double extra[4] = {0.0, 0.0, 0.0, 0.0};  // |g|^2, <x', p^>
+    if (ok) {
+        const double2 *rc = A.e->coef[C_ROT], *gc = A.e->coef[C_GRAD];
+        Cx<double> x[12], pp[12], t[12], xr[12];
+        load_site(A.x, A.F, par, cb, x);
+        load_site(A.p, A.F, par, cb, pp);
+        site_mac(xr, rc[0], x, true);
+        site_mac(xr, rc[1], pp, false);
+        store_site(A.x, A.F, par, cb, xr);
+        site_dot(xr, pp, extra[2], extra[3]);
+        load_site(A.y, A.F, par, cb, x);  // y
+        load_site(A.z, A.F, par, cb, t);  // z
+        site_mac(pp, rc[0], x, true);      // y'
+        site_mac(pp, rc[1], t, false);
+        store_site(A.y, A.F, par, cb, pp);
+        site_mac(g, gc[0], pp, true);
+        site_mac(g, gc[1], xr, false);
+        store_site(A.g, A.F, par, cb, g);
+        site_dot_re(g, g, extra[0]);
+    }
+    basis_partials(A, ok, par, cb, g, extra, sh);
+}
+
+__global__ void __launch_bounds__(kBlk, 2) proj_dir_dots_kernel(const __grid_constant__ StepArgs A) {
+    __shared__ double sh[kBlk / 32][2 * kDotGroup];
+    if (A.e->halt || A.e->stop) return;  // the same for every block
+    int par, cb;
+    const bool ok = site(A.F, par, cb);
+    double v[2 * kDotGroup] = {};
+    if (ok) {
+        const double2 *pc = A.e->coef[C_PROJ], *dc = A.e->coef[C_DIR];
+        Cx<double> acc[12], t[12];
+        // g' = sum_k C_PROJ[k] {g, v_0, .., v_{j-1}}_k (g itself when j = 0)
+        load_site(A.g, A.F, par, cb, t);
+        site_mac(acc, A.j > 0 ? pc[0] : make_double2(1.0, 0.0), t, true);
+        for (int i = 0; i < A.j; ++i) {
+            load_site(A.v[i], A.F, par, cb, t);
+            site_mac(acc, pc[1 + i], t, false);
+        }
+        // p = sum_k C_DIR[k] {g', p, x}_k, the first term scaled in place
+        if (!(dc[0].x == 1.0 && dc[0].y == 0.0)) {
+            const Cx<double> w = {dc[0].x, dc[0].y};
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const Cx<double> g = acc[c];
+                acc[c] = {0.0, 0.0};
+                cmac(acc[c], w, g);
+            }
+        }
+        load_site(A.p, A.F, par, cb, t);
+        site_mac(acc, dc[1], t, false);
+        load_site(A.x, A.F, par, cb, t);
+        site_mac(acc, dc[2], t, false);
+        store_site(A.p, A.F, par, cb, acc);
+        site_dot(t, acc, v[0], v[1]);  // <x, p>
+        site_dot_re(acc, acc, v[2]);   // |p|^2
+    }
+    group_partials(v, 0, 2, A.partials, A.nb, sh);
 }
 
 // Eigen-decomposition of the Hermitian n x n matrix H (row-major, destroyed)
@@ -509,9 +715,11 @@ cola_status normalize(Ctx &c, char *x) {
 
 // ------------------------------------------------ device-driven minimisation --
 // Launches on stream st (capturing or not) with results left on the device.
-void dots_dev(Ctx &c, cudaStream_t st, const std::vector<std::pair<const char *, const char *>> &ab) {
+void dots_dev(Ctx &c, cudaStream_t st, const std::vector<std::pair<const char *, const char *>> &ab,
+              unsigned re_only = 0) {
     DotArgs A;
     std::memset(&A, 0, sizeof(A));
+    A.re_only = re_only;
     A.F = c.F;
     A.n = (int)ab.size();
     for (int k = 0; k < A.n; ++k) {
@@ -540,6 +748,45 @@ void comb_dev(Ctx &c, cudaStream_t st, char *out, const std::vector<const char *
 template <int STEP>
 void ctl(Ctx &c, cudaStream_t st, const CtlParams &p, cudaGraphConditionalHandle h = 0) {
     eig_ctl_kernel<STEP><<<1, 1, 0, st>>>(c.e, c.dres, p, h);
+}
+
+// The dots' block partials only (a fin_ctl launch finishes them).
+void dots_part(Ctx &c, cudaStream_t st, const std::vector<std::pair<const char *, const char *>> &ab,
+               unsigned re_only = 0) {
+    DotArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.re_only = re_only;
+    A.F = c.F;
+    A.n = (int)ab.size();
+    for (int k = 0; k < A.n; ++k) {
+        A.a[k] = ab[k].first;
+        A.b[k] = ab[k].second;
+    }
+    A.partials = c.partials;
+    A.nb = c.nb;
+    dots_kernel<<<c.nb, kBlk, 0, st>>>(A);
+}
+
+template <int STEP>
+void fin_ctl(Ctx &c, cudaStream_t st, int n, const CtlParams &p, cudaGraphConditionalHandle h = 0) {
+    fin_ctl_kernel<STEP><<<1, kBlk, 0, st>>>(c.e, c.partials, c.nb, n, c.dres, p, h);
+}
+
+StepArgs step_args(Ctx &c, int j, char *x) {
+    StepArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.F = c.F;
+    A.j = j;
+    A.x = x;
+    A.y = c.x_y;
+    A.g = c.g_;
+    A.p = c.p;
+    A.z = c.z;
+    for (int i = 0; i < j; ++i) A.v[i] = c.V[i];
+    A.e = c.e;
+    A.partials = c.partials;
+    A.nb = c.nb;
+    return A;
 }
 
 // {<v_i, f>} for i < j, then |f|^2, then the extra pairs
@@ -593,18 +840,19 @@ cola_status build_ritz_graph(Ctx &c, int j, const CtlParams &p, cudaGraphExec_t 
         ctl<CTL_PROJ>(c, cs, p);
         comb_dev(c, cs, x, with_basis(c, j, x), C_PROJ, 1);
     }
-    dots_dev(c, cs, {{x, x}});
+    dots_dev(c, cs, {{x, x}}, 1u);
     ctl<CTL_NORM>(c, cs, p);
     comb_dev(c, cs, x, {x}, C_NORM, 1);
     st = apply_mdagm(c.g, COLA_F64, c.op, y, x, c.t, c.mp, 1, nullptr, false, cs);
     if (st == COLA_OK) {
-        dots_dev(c, cs, {{x, y}});
+        dots_dev(c, cs, {{x, y}}, 1u);  // mu: the real part
         ctl<CTL_MU>(c, cs, p);
         comb_dev(c, cs, g, {y, x}, C_GRAD, 1);
-        dots_dev(c, cs, against_basis(c, j, g));
+        dots_dev(c, cs, against_basis(c, j, g), j < 32 ? 1u << j : 0u);  // |g|^2 real
         ctl<CTL_GRAD0>(c, cs, p);
         if (j > 0) comb_dev(c, cs, g, with_basis(c, j, g), C_PROJ, 1);
         st = cuda_check(cudaMemcpyAsync(pp, g, c.fb, cudaMemcpyDeviceToDevice, cs), "p = g");
+        if (st == COLA_OK) dots_part(c, cs, {{x, pp}, {pp, pp}});  // the loop's first step starts from these
     }
     if (st == COLA_OK) {
         ctl<CTL_LOOP0>(c, cs, p, h);
@@ -636,7 +884,7 @@ cola_status build_ritz_graph(Ctx &c, int j, const CtlParams &p, cudaGraphExec_t 
     }
     // epilogue: normalise v_j
     if (st == COLA_OK) {
-        dots_dev(c, cs, {{x, x}});
+        dots_dev(c, cs, {{x, x}}, 1u);
         ctl<CTL_NORM>(c, cs, p);
         comb_dev(c, cs, x, {x}, C_NORM, 1);
         st = cuda_check(cudaGetLastError(), "eigensolver epilogue");
@@ -651,23 +899,15 @@ cola_status build_ritz_graph(Ctx &c, int j, const CtlParams &p, cudaGraphExec_t 
     if ((st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                          "capture")) != COLA_OK)
         return fail(st);
-    dots_dev(c, cs, {{x, pp}, {pp, pp}});
-    ctl<CTL_PERP>(c, cs, p);
+    fin_ctl<CTL_PERP>(c, cs, 2, p);  // <x, p>, |p|^2: partials of the prologue or of the previous step
     comb_dev(c, cs, pp, {pp, x}, C_PERP, 3);
     st = apply_mdagm(c.g, COLA_F64, c.op, z, pp, c.t, c.mp, 1, nullptr, false, cs);  // z = A p = pn A p^
     if (st == COLA_OK) {
-        dots_dev(c, cs, {{x, z}, {pp, z}});
-        ctl<CTL_ROT>(c, cs, p);
-        comb_dev(c, cs, x, {x, pp}, C_ROT, 3);
-        comb_dev(c, cs, y, {y, z}, C_ROT, 3);
-        comb_dev(c, cs, g, {y, x}, C_GRAD, 3);
-        std::vector<std::pair<const char *, const char *>> ab = against_basis(c, j, g);
-        ab.push_back({x, pp});
-        dots_dev(c, cs, ab);
-        ctl<CTL_GRAD>(c, cs, p);
-        if (j > 0) comb_dev(c, cs, g, with_basis(c, j, g), C_PROJ, 3);
-        comb_dev(c, cs, pp, {g, pp, x}, C_DIR, 3);
-        ctl<CTL_END>(c, cs, p, h);
+        dots_part(c, cs, {{x, z}, {pp, z}}, 3u);  // the line search uses the real parts
+        fin_ctl<CTL_ROT>(c, cs, 2, p);
+        rot_grad_dots_kernel<<<c.nb, kBlk, 0, cs>>>(step_args(c, j, x));  // x, y, g; <v_i, g>, |g|^2, <x, p>
+        fin_ctl<CTL_GRAD>(c, cs, j + 2, p, h);                            // and CTL_END: the loop condition
+        proj_dir_dots_kernel<<<c.nb, kBlk, 0, cs>>>(step_args(c, j, x));  // p; <x, p>, |p|^2
         st = cuda_check(cudaGetLastError(), "eigensolver step");
     }
     {
