@@ -653,7 +653,6 @@ def run_cola(args):
     copy = torch.cuda.Stream(device=dev)
     main = torch.cuda.current_stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(2)]
-    keep = []
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     with torch.cuda.stream(copy):
@@ -675,10 +674,11 @@ def run_cola(args):
         copy.wait_stream(main)
         with torch.cuda.stream(copy):
             x_host[cur].copy_(xe, non_blocking=True)
-        keep.append(xe)
+        # the caching allocator may reuse x's memory once the copy stream has read it
+        xe.record_stream(copy)
+        del xe
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - w0) / e2e_steps
-    del keep
     e2e_ms, e2e_flops = aggregate_ranks(e2e_s * 1e3, FLOP_PER_SITE * vh * e2e_ds / e2e_steps, dev)
     e2e_s = e2e_ms * 1e-3
     e2e_value = e2e_flops / e2e_s / 1e9
