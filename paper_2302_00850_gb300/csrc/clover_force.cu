@@ -43,6 +43,56 @@ __device__ __forceinline__ int plane_of(int mu, int nu) {  // mu < nu
     return mu == 0 ? nu - 1 : mu == 1 ? nu + 1 : 5;
 }
 
+// lam += s P for one entry s of sigma: an exact zero, a pure real or a pure
+// imaginary s (all entries of sigma in the chirality blocks are one of
+// these) takes 0 or 2 FP64 multiply-adds, a general one 4
+__device__ __forceinline__ void sigma_mac(C64 &lam, double sr, double si, const C64 &P) {
+    if (si == 0.0) {
+        if (sr == 0.0) return;
+        lam.re = fma(sr, P.re, lam.re);
+        lam.im = fma(sr, P.im, lam.im);
+    } else if (sr == 0.0) {
+        lam.re = fma(-si, P.im, lam.re);
+        lam.im = fma(si, P.re, lam.im);
+    } else {
+        lam.re = fma(sr, P.re, fma(-si, P.im, lam.re));
+        lam.im = fma(sr, P.im, fma(si, P.re, lam.im));
+    }
+}
+
+// The spin products of colour entry (b, a) of Lam: P[chi][s][t] = X_tb conj(Y_sa)
+// within chirality block chi (spin index 2 chi + s, 2 chi + t).
+__device__ __forceinline__ void spin_products(const C64 (&x)[12], const C64 (&y)[12], int b, int a,
+                                              C64 (&P)[2][2][2]) {
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const C64 xv = x[(2 * chi + t) * 3 + b], yv = y[(2 * chi + s) * 3 + a];
+                P[chi][s][t] = {fma(xv.re, yv.re, xv.im * yv.im), fma(xv.im, yv.re, -xv.re * yv.im)};
+            }
+}
+
+// Lam_p[b][a] = sum over chi, s, t of sigma_p[chi][s][t] P[chi][s][t]
+__device__ __forceinline__ C64 plane_entry(const CloverSigma &sig, int p, const C64 (&P)[2][2][2]) {
+    C64 lam = {0.0, 0.0};
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                sigma_mac(lam, sig.v[p][chi][2 * s + t][0], sig.v[p][chi][2 * s + t][1], P[chi][s][t]);
+    return lam;
+}
+
+// Gam_p = L + L^dag with L = Lam_p - tr Lam_p / 3 and
+//   Lam_p[b][a] = sum over the chirality blocks of sigma_st X_tb conj(Y_sa).
+// The 8 spin products of a colour entry serve all six planes, and of Lam
+// only what Gam needs is formed: the real diagonal, and each off-diagonal
+// pair (b, a), (a, b) together.
 __global__ void __launch_bounds__(128) clover_gamma_kernel(const Geom g, const CloverSigma sig, const double2 *X,
                                                            const double2 *Y, double *gam) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,41 +104,35 @@ __global__ void __launch_bounds__(128) clover_gamma_kernel(const Geom g, const C
         x[c] = {a.x, a.y};
         y[c] = {b.x, b.y};
     }
+    double dg[6][3];
+    C64 P[2][2][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        spin_products(x, y, b, b, P);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) dg[p][b] = plane_entry(sig, p, P).re;
+    }
+    const size_t V = g.V;
+    constexpr int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        C64 Q[2][2][2];
+        spin_products(x, y, pairs[q][0], pairs[q][1], P);  // (b, a)
+        spin_products(x, y, pairs[q][1], pairs[q][0], Q);  // (a, b)
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const C64 ba = plane_entry(sig, p, P), ab = plane_entry(sig, p, Q);
+            double *o = gam + (size_t)p * kGamReals * V + i;
+            o[(2 + 2 * q) * V] = ba.re + ab.re;
+            o[(3 + 2 * q) * V] = ba.im - ab.im;
+        }
+    }
+#pragma unroll
     for (int p = 0; p < 6; ++p) {
-        C64 lam[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) lam[k] = {0.0, 0.0};
-        // Lam_ba = sum over the chirality blocks of sigma_st X_tb conj(Y_sa)
-#pragma unroll
-        for (int chi = 0; chi < 2; ++chi)
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const C64 sg = {sig.v[p][chi][2 * s + t][0], sig.v[p][chi][2 * s + t][1]};
-                    if (sg.re == 0.0 && sg.im == 0.0) continue;
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        const C64 sx = cmul(sg, x[(2 * chi + t) * 3 + b]);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const C64 v = cmulc(sx, y[(2 * chi + s) * 3 + a]);
-                            lam[3 * b + a].re += v.re;
-                            lam[3 * b + a].im += v.im;
-                        }
-                    }
-                }
-        // Gam = L + L^dag, L = Lam - tr Lam / 3: the trace only moves the diagonal
-        const double tr = (lam[0].re + lam[4].re + lam[8].re) / 3.0;
-        double *o = gam + (size_t)p * kGamReals * g.V + i;
-        o[0 * (size_t)g.V] = 2.0 * (lam[0].re - tr);
-        o[1 * (size_t)g.V] = 2.0 * (lam[4].re - tr);
-        o[2 * (size_t)g.V] = lam[1].re + lam[3].re;  // (0,1)
-        o[3 * (size_t)g.V] = lam[1].im - lam[3].im;
-        o[4 * (size_t)g.V] = lam[2].re + lam[6].re;  // (0,2)
-        o[5 * (size_t)g.V] = lam[2].im - lam[6].im;
-        o[6 * (size_t)g.V] = lam[5].re + lam[7].re;  // (1,2)
-        o[7 * (size_t)g.V] = lam[5].im - lam[7].im;
+        const double tr = (dg[p][0] + dg[p][1] + dg[p][2]) / 3.0;
+        double *o = gam + (size_t)p * kGamReals * V + i;
+        o[0] = 2.0 * (dg[p][0] - tr);
+        o[V] = 2.0 * (dg[p][1] - tr);
     }
 }
 
