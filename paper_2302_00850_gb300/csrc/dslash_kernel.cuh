@@ -731,9 +731,17 @@ __device__ __forceinline__ void block_row_sum(double v, bool write, double *dst)
 #ifndef COLA_STAGED_MINB
 #define COLA_STAGED_MINB 5
 #endif
-// depth of the staged pipeline (hops in flight per thread)
+// depth of the staged pipeline: while a thread computes one hop, the next
+// stages - 1 are in flight.  With the 16 + 8 byte FP16 links, 4 stages ran
+// the plain 32^3x64 parity apply in 67.0 us against 69.6 us for 3 (5 blocks
+// of 39 KB per SM), while the even-odd operator (two of its four launches
+// with the xpay epilogue) and the clover operator were no faster or slower
+// with 4: the plain hop takes 4 stages, the other epilogues COLA_STAGES.
 #ifndef COLA_STAGES
 #define COLA_STAGES 3
+#endif
+#ifndef COLA_STAGES_HOP
+#define COLA_STAGES_HOP 4
 #endif
 template <int P, int NS>
 struct LaunchShape {
@@ -954,7 +962,7 @@ static cudaError_t launch_t(const DslashArgs &A, int nparity, int bx, int nb, cu
         return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
     } else {
         if (staged_depth(P) == 0) return launch_ns<P, RECON, DAGGER, EPI, 0>(A, nparity, bx, nb, s);
-        return launch_ns<P, RECON, DAGGER, EPI, COLA_STAGES>(A, nparity, bx, nb, s);
+        return launch_ns<P, RECON, DAGGER, EPI, EPI == EPI_HOP ? COLA_STAGES_HOP : COLA_STAGES>(A, nparity, bx, nb, s);
     }
 }
 
