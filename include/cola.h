@@ -137,8 +137,7 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
                              int nrhs, cudaStream_t stream);
 
 /* The same operator as cola_mdagm_apply, for callers that cannot allocate
- * device memory when they call it (for example code being captured into a
- * CUDA graph, where cudaMalloc is not allowed, or a service that reserves all
+ * device memory when they call it (for example a service that reserves all
  * device memory up front).  The paper has no counterpart: it is an addition
  * of this library.  It calls no allocator; its temporaries live in one
  * static device array of 64 MiB that the library holds on each device until
@@ -147,7 +146,7 @@ cola_status cola_mdagm_apply(cola_gauge g, void *out, const void *in, int op, co
  * the array's device address in the current device's context
  * (cudaGetSymbolAddress), so a context that was reset and created again gets
  * the new address; the first call in a context may load the library's device
- * code there, so make that first call before any stream capture.  With
+ * code there.  With
  * lazy module loading (the CUDA default) the array is reserved on a device
  * when this part of the library is first used there; with
  * CUDA_MODULE_LOADING=EAGER every process that loads the library reserves it

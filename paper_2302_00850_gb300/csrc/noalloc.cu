@@ -2,11 +2,9 @@
 // allocation, for callers that cannot allocate device memory at the time of
 // the call.
 //
-// Typical such callers: code that is being captured into a CUDA graph
-// (cudaMalloc is not allowed while a stream is capturing), code that runs
-// where a device allocation would implicitly synchronise the GPU or must not
-// fail (a fixed-memory service, a callback), or a host program that reserves
-// all device memory up front.  cola_mdagm_apply allocates its two
+// Typical such callers: code that runs where a device allocation would
+// implicitly synchronise the GPU or must not fail (a fixed-memory service, a
+// callback), or a host program that reserves all device memory up front.  cola_mdagm_apply allocates its two
 // temporaries in the gauge handle on first use; this variant instead uses
 // one file-scope device array of fixed size, kStaticScratchBytes (64 MiB),
 // that lives in the library's device image.  A GPU that has loaded this part

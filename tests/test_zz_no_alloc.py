@@ -1,8 +1,8 @@
 """cola_mdagm_apply_noalloc: the allocation-free normal operator (GPU).
 
-Some callers cannot allocate device memory when they call the library (code
-being captured into a CUDA graph, or a service that reserves all device
-memory up front).  This entry point runs M^dag M out of a static 64 MiB
+Some callers cannot allocate device memory when they call the library (a
+service that reserves all device memory up front, a callback that must not
+fail).  This entry point runs M^dag M out of a static 64 MiB
 device array instead of allocating.  Here it is called through the C ABI and
 compared with cola_mdagm_apply on two calls in a row, with different inputs,
 operators and precisions, so that anything the first call left in the shared
