@@ -33,8 +33,9 @@
 // vector index, built on first use in a call).  A CG step is 7 launches
 // besides the operator: the rotation, the gradient and its dot products
 // share one pass over the sites, as do the projection, the new direction and
-// the dot products the next step starts from.  The host launches the graphs of a sweep back to back, runs the
-// Rayleigh-Ritz step, and reads the residuals once per sweep.
+// the dot products the next step starts from.  The host launches the graphs
+// of a sweep back to back, runs the Rayleigh-Ritz step, and reads the
+// residuals once per sweep.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
